@@ -1,0 +1,172 @@
+"""Oracle: rows of the impedance matrix [M + S] (Section 2.1, Eqs. 3-8).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Discrete problem (Eq. 3): [M + S] p = s on an n_x x n_y x n_z grid, unknowns
+ordered lexicographically with x fastest (row r = ix + n_x (iy + n_y iz)),
+constant density b = 1 (Section 3.1), kappa = v^2, exp(-i omega t).  Points
+outside the grid are zero (Dirichlet behind the PML); stencil entries that
+would reach them are dropped.
+
+Stiffness (Eq. 4: S = ws1 S1 + ws2/3 sum S2,i + ws3/4 sum S3,i).  The paper
+names two equivalent constructions (rotated-coordinate staggered grids, or
+the "average-derivative" mixed stencil of Min et al. 2000 / Chen 2012); the
+explicit rotated-frame PML handling is not in the text.  Reading used here:
+
+    S p = sum_{d in x,y,z}  T_d [ delta_d p ]
+
+* delta_d is the stretched second difference along d (see ``pml``):
+  delta_x p(i) = [ (p(i+1)-p(i))/xi(i+1/2) - (p(i)-p(i-1))/xi(i-1/2) ] / (xi(i) h^2)
+* T_d averages over the 3x3 plane transverse to d with the row's weights:
+  centre t0 = ws1 + 2 ws2/3 + ws3/2, each of the 4 in-plane face neighbours
+  t1 = ws2/12, each of the 4 in-plane corners t2 = ws3/8.
+
+In the interior (xi = 1) this gives the class coefficients
+  c0 = -6 t0/h^2, c_face = (t0 - ws2/3)/h^2, c_edge = (ws2/6 - ws3/4)/h^2,
+  c_corner = 3 ws3/(8 h^2),
+which equal ws1 x (7-point) + ws2 x (the average of the three rotated 11-point
+stencils) + ws3 x (the average of the four diagonal stencils): their
+plane-wave symbol is -(2/h^2) X with X the radicand of Eq. vtilde.
+
+Mass: second form of Eq. 8 (kappa at the collocation point; its second sum
+must run over 12 points): (omega^2/v_0^2) [wm1 p0 + wm2 sum_6 faces +
+wm3 sum_12 edges + wm4 sum_8 corners], per-point weights (see ``weights``).
+For the complex-shifted Laplacian used by the GPU preconditioner omega^2 is
+replaced by (1 + i beta) omega^2 (beta = 0 is the paper's operator).
+
+Weights per row (GA stencil, Section 3.1): interpolated in the table at the
+row's own 1/G = f h / v.
+
+Pins (tests/test_oracle_operator.py): interior symbol == m J - 2X/h^2 on a
+periodic box (Eq. vtilde, independent formulas); stiffness annihilates
+constants and linear fields and maps x^2+y^2+z^2 to 6; ws=(1,0,0), wm=(1,0,0,0)
+gives the Kronecker-sum 7-point Laplacian with PML (scipy.sparse.kron); a
+homogeneous model with any weights equals a Kronecker assembly of
+delta_d (x) T_d; every row of a heterogeneous model equals the row of the
+homogeneous model with that row's velocity.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import pml as _pml
+from . import weights as _w
+
+OFFSETS = tuple(itertools.product((-1, 0, 1), repeat=3))   # (dk, dj, di)
+
+
+def axis_coefficients(prof, n, h, omega):
+    """Per-node coefficients of delta_d towards i+1 (up) and i-1 (dn)."""
+    xi_i, xi_h = _pml.xi_nodes(prof, n, h, omega)
+    up = 1.0 / (xi_i * xi_h[1:] * h * h)
+    dn = 1.0 / (xi_i * xi_h[:-1] * h * h)
+    return up, dn
+
+
+def profiles_for(shape, h, npml, v_ref, r_coef):
+    """Physical profiles (x, y, z) for a grid of shape (nz, ny, nx) with
+    npml = (x_lo, x_hi, y_lo, y_hi, z_lo, z_hi) nodes."""
+    nz, ny, nx = shape
+    return (_pml.Profile1D.from_grid(nx, h, npml[0], npml[1], v_ref, r_coef),
+            _pml.Profile1D.from_grid(ny, h, npml[2], npml[3], v_ref, r_coef),
+            _pml.Profile1D.from_grid(nz, h, npml[4], npml[5], v_ref, r_coef))
+
+
+def row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows=None, beta=0.0):
+    """27 complex coefficients for the requested rows.
+
+    v: float array (nz, ny, nx); rows: flat row indices (None = all rows).
+    Returns coef of shape (len(rows), 27) in OFFSETS order (dk, dj, di) and the
+    validity mask (neighbour inside the grid)."""
+    nz, ny, nx = v.shape
+    omega = 2.0 * np.pi * f
+    if rows is None:
+        rows = np.arange(nx * ny * nz)
+    rows = np.asarray(rows, dtype=np.int64)
+    ix = rows % nx
+    iy = (rows // nx) % ny
+    iz = rows // (nx * ny)
+    v0 = v.reshape(-1)[rows].astype(np.float64)
+
+    w = _w.lookup(table, inv_g_nodes, f * h / v0)
+    ws1, ws2, ws3, wm1, wm2, wm3, wm4 = (w[:, k] for k in range(7))
+    tw = (ws1 + 2.0 * ws2 / 3.0 + 0.5 * ws3, ws2 / 12.0, ws3 / 8.0)   # T_d weights
+    mu = (wm1, wm2, wm3, wm4)                                        # mass per class
+    m = (1.0 + 1j * beta) * omega ** 2 / v0 ** 2
+
+    ux, dx = axis_coefficients(profiles[0], nx, h, omega)
+    uy, dy = axis_coefficients(profiles[1], ny, h, omega)
+    uz, dz = axis_coefficients(profiles[2], nz, h, omega)
+
+    def second(up, dn, i, s):
+        if s == 1:
+            return up[i]
+        if s == -1:
+            return dn[i]
+        return -(up[i] + dn[i])
+
+    coef = np.zeros((rows.size, 27), dtype=np.complex128)
+    valid = np.zeros((rows.size, 27), dtype=bool)
+    for k, (sk, sj, si) in enumerate(OFFSETS):
+        c = (tw[abs(sj) + abs(sk)] * second(ux, dx, ix, si)
+             + tw[abs(si) + abs(sk)] * second(uy, dy, iy, sj)
+             + tw[abs(si) + abs(sj)] * second(uz, dz, iz, sk)
+             + m * mu[abs(si) + abs(sj) + abs(sk)])
+        coef[:, k] = c
+        valid[:, k] = ((ix + si >= 0) & (ix + si < nx) & (iy + sj >= 0) & (iy + sj < ny)
+                       & (iz + sk >= 0) & (iz + sk < nz))
+    return coef, valid
+
+
+def assemble_csr(v, h, f, profiles, table, inv_g_nodes, beta=0.0):
+    """The impedance matrix as scipy CSR (complex128), 27 entries per row
+    (fewer at the grid edges)."""
+    nz, ny, nx = v.shape
+    N = nx * ny * nz
+    rows = np.arange(N)
+    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta)
+    cols = np.empty((N, 27), dtype=np.int64)
+    for k, (sk, sj, si) in enumerate(OFFSETS):
+        cols[:, k] = rows + si + nx * (sj + ny * sk)
+    r = np.repeat(rows, 27).reshape(N, 27)
+    A = sp.csr_matrix((coef[valid], (r[valid], cols[valid])), shape=(N, N))
+    A.sort_indices()
+    return A
+
+
+def apply_rows(v, h, f, profiles, table, inv_g_nodes, x, rows, beta=0.0):
+    """(A x) at the requested rows only, x of shape (R, nz, ny, nx); returns
+    (R, len(rows)).  Used to check full-size GPU applies on sampled outputs."""
+    nz, ny, nx = v.shape
+    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta)
+    rows = np.asarray(rows, dtype=np.int64)
+    ix = rows % nx
+    iy = (rows // nx) % ny
+    iz = rows // (nx * ny)
+    xf = x.reshape(x.shape[0], -1)
+    out = np.zeros((x.shape[0], rows.size), dtype=np.complex128)
+    for k, (sk, sj, si) in enumerate(OFFSETS):
+        ok = valid[:, k]
+        col = (ix + si) + nx * ((iy + sj) + ny * (iz + sk))
+        col = np.where(ok, col, 0)
+        out += np.where(ok, coef[:, k], 0.0)[None, :] * xf[:, col]
+    return out
+
+
+def interior_class_coefficients(w7, h, omega, v, beta=0.0):
+    """(c0, c_face, c_edge, c_corner) of an interior row (xi = 1) written out
+    from the class decomposition of Eq. 4: ws1 x 7-point, ws2 x mean of the
+    three 11-point stencils, ws3 x mean of the four diagonal stencils, plus the
+    mass of Eq. 8 -- an independent route to the same numbers as
+    ``row_coefficients`` away from the PML."""
+    ws1, ws2, ws3, wm1, wm2, wm3, wm4 = w7
+    m = (1.0 + 1j * beta) * omega ** 2 / v ** 2
+    # class stencils (centre, face, edge, corner) times h^2
+    s1 = (-6.0, 1.0, 0.0, 0.0)
+    s2 = (-4.0, 1.0 / 3.0, 1.0 / 6.0, 0.0)
+    s3 = (-3.0, 0.5, -0.25, 3.0 / 8.0)
+    mass = (wm1, wm2, wm3, wm4)
+    return tuple((ws1 * s1[k] + ws2 * s2[k] + ws3 * s3[k]) / h ** 2 + m * mass[k] for k in range(4))

@@ -1,0 +1,43 @@
+"""Pins of the textbook multigrid pieces (not in the paper)."""
+import numpy as np
+import scipy.sparse as sp
+
+from oracle import multigrid as MG
+
+
+def test_prolongation_exact_on_trilinear_functions():
+    shape = (9, 7, 11)          # odd: coarse nodes on both ends
+    cz, cy, cx = MG.coarse_shape(shape)
+    Z, Y, X = np.meshgrid(np.arange(cz) * 2.0, np.arange(cy) * 2.0, np.arange(cx) * 2.0, indexing="ij")
+    f = lambda x, y, z: 1 + 2 * x - y + 0.5 * z + 0.25 * x * y - z * x + 0.1 * x * y * z
+    fine = MG.prolong(f(X, Y, Z)[None], shape)[0]
+    z, y, x = np.meshgrid(*(np.arange(n, dtype=float) for n in shape), indexing="ij")
+    assert np.allclose(fine, f(x, y, z), atol=1e-12)
+
+
+def test_restriction_is_scaled_transpose_and_weights():
+    shape = (5, 6, 7)
+    R = MG.restriction_matrix(shape)
+    P = MG.prolongation_matrix(shape)
+    assert abs(R - P.T / 8).max() == 0
+    # an interior coarse node sees 1/8, 1/16, 1/32, 1/64 on 1, 6, 12, 8 fine nodes
+    nz, ny, nx = shape
+    cz, cy, cx = MG.coarse_shape(shape)
+    I = 1 + cx * (1 + cy * 1)
+    row = R.getrow(I).toarray().ravel()
+    vals = np.sort(row[row > 0])
+    assert np.allclose(np.unique(vals), [1 / 64, 1 / 32, 1 / 16, 1 / 8])
+    assert np.isclose(row.sum(), 1.0)
+
+
+def test_jacobi_fixed_point():
+    rng = np.random.default_rng(0)
+    n = 30
+    A = sp.diags([rng.uniform(4, 5, n) + 1j, -np.ones(n - 1), -np.ones(n - 1)], [0, 1, -1]).tocsr()
+    b = rng.normal(size=(2, n)) + 0j
+    x = np.linalg.solve(A.toarray(), b.T).T
+    assert np.allclose(MG.jacobi_sweep(A, x, b, 0.7), x, atol=1e-13)
+    y = np.zeros_like(b)
+    for _ in range(200):
+        y = MG.jacobi_sweep(A, y, b, 0.8)
+    assert np.allclose(y, x, atol=1e-10)
