@@ -1,0 +1,158 @@
+/*
+ * hx27 -- wavelength-adaptive 27-point Helmholtz operator and solver (C ABI).
+ *
+ * Method: Aghamiry, Gholami, Combe & Operto, "Accurate 3D frequency-domain
+ * seismic wave modeling with the wavelength-adaptive 27-point finite-difference
+ * stencil" (arXiv 2108.08730).  The discrete problem is [M + S] p = s (Eq. 3)
+ * on a regular grid with PML (Eqs. 1.1-1.4), constant density (Section 3.1),
+ * stiffness weights (ws1, ws2, ws3) and consistent-mass weights (wm1..wm4)
+ * picked per row from a Tikhonov-smoothed table by the row's own
+ * G = v / (f h) (Section 2.2; the GA stencil of Section 3.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Grids are row-major with x fastest: index = ix + nx*(iy + ny*iz).
+ *    Velocity is float32 v[nz][ny][nx] in m/s.  Wavefields are interleaved
+ *    complex (re, im): complex64 = 2 x float32, complex128 = 2 x float64,
+ *    laid out [nrhs][nz][ny][nx].
+ *  - Pointers named *_dev are device pointers on the context's device,
+ *    *_host are host pointers.  All buffers passed in are owned by the
+ *    caller; the library never frees or retains them past the call (device
+ *    work is enqueued on `stream` and may still be running when the call
+ *    returns, like any CUDA launch).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *  - The context owns its caches (weight table on the device, PML
+ *    coefficient arrays, multigrid hierarchies, Krylov workspaces) and frees
+ *    them in hx_ctx_destroy.  A context is not thread-safe; use one per host
+ *    thread.
+ *  - Every call returns an hx_status; on failure it also records a message
+ *    retrievable with hx_last_error.  Nothing throws across the ABI.
+ */
+#ifndef HX27_H
+#define HX27_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HX_OK = 0,
+  HX_ERR_ARG = -1,            /* invalid argument (message says which)          */
+  HX_ERR_OOM = -2,            /* device or host allocation failed               */
+  HX_ERR_NOT_CONVERGED = -3,  /* solve stopped at its iteration cap; the best
+                                 iterate is in the output and the report filled */
+  HX_ERR_NUMERIC = -4,        /* NaN/Inf or breakdown detected                  */
+  HX_ERR_TIMEOUT = -5,        /* a bounded device wait ran out                  */
+  HX_ERR_CUDA = -6,           /* a CUDA runtime call failed                     */
+  HX_ERR_STATE = -7           /* call order (e.g. no weight table set yet)      */
+} hx_status;
+
+typedef struct hx_ctx hx_ctx;
+
+/* Grid, frequency and PML of one problem.  PML nodes are part of the grid
+ * (npml nodes at each face).  The damping follows the reading
+ * gamma(d) = gamma0 (d/L)^2, gamma0 = 3 v_ref / (2 L) ln(1/r_coef), with d the
+ * distance from the inner PML face and L = npml h; xi = 1 + i gamma/omega
+ * (Eqs. 1.1-1.4, exp(-i omega t)).  Outside the grid the field is zero. */
+typedef struct {
+  int nx, ny, nz;      /* nodes per axis incl. PML, each >= 3              */
+  double h;            /* grid interval (m), > 0                            */
+  double f;            /* frequency (Hz), > 0                               */
+  int npml[6];         /* x_lo, x_hi, y_lo, y_hi, z_lo, z_hi; 0 <= npml < n/2 */
+  double v_ref;        /* PML reference speed (m/s), > 0; normally max(v)   */
+  double r_coef;       /* PML target reflection coefficient in (0, 1)      */
+} hx_grid;
+
+/* A grid-node point source (Section 3.1: s = delta(x - x_s)) of complex
+ * amplitude (amp_re, amp_im) for right-hand side `rhs`.  Several sources may
+ * feed the same rhs.  Injected as amp / h^3 at the node, or spread over the 27
+ * nodes with the row's consistent-mass weights when hx_solve_opts.source_spread
+ * is 1 (a reading: it cancels the 1/(1-(kh)^2/12) far-field amplitude bias of
+ * the plain delta).  Sources must lie inside the grid. */
+typedef struct {
+  int ix, iy, iz;
+  int rhs;
+  double amp_re, amp_im;
+} hx_source;
+
+/* ---------------------------------------------------------------- weights */
+
+/* Fit the adaptive weight table (Section 2.2): for 1/G on the uniform grid
+ * 0, d_inv_g, ..., inv_g_max (n_g = round(inv_g_max/d_inv_g) + 1 nodes) and
+ * plane waves at every (theta, phi) pair of the given angle lists (degrees),
+ * minimise ||H w - g||^2 + lambda ||D P w||^2 over the 5 free weights per
+ * node, with H, g of Eq. linear_basic (H2 with the constant term derived from
+ * Eq. vtilde), D the first-order forward difference along 1/G of each weight
+ * series and P the series-major permutation.  Solved in FP64 by sequential
+ * Givens QR of the stacked banded system (no normal equations).
+ *   table_out: caller-owned host array of capacity doubles; receives
+ *              n_g rows of 7: [ws1, ws2, ws3, wm1, wm2, wm3, wm4] with
+ *              PER-POINT mass weights (wm1 + 6 wm2 + 12 wm3 + 8 wm4 = 1).
+ *   n_g_out:   receives n_g (also when capacity is too small, with HX_ERR_ARG).
+ * Needs no context and no GPU.  Errors: HX_ERR_ARG (bad sizes, lambda <= 0,
+ * capacity < 7 n_g), HX_ERR_NUMERIC (rank-deficient system). */
+int hx_build_weight_table(const double* theta_deg, int n_theta,
+                          const double* phi_deg, int n_phi,
+                          double inv_g_max, double d_inv_g, double lambda,
+                          double* table_out, int capacity, int* n_g_out);
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context bound to CUDA device `device`.  *out is NULL on failure. */
+int hx_ctx_create(hx_ctx** out, int device);
+void hx_ctx_destroy(hx_ctx* ctx);
+/* Message of the last failed call on ctx (static "" when none; "no context"
+ * for ctx == NULL).  Valid until the next call on ctx. */
+const char* hx_last_error(const hx_ctx* ctx);
+
+/* Install the weight table used by every later operator call on ctx:
+ * table_host [n_g][7] as produced by hx_build_weight_table, nodes at
+ * 1/G = i * d_inv_g.  Copied (FP64 and FP32 forms) to the device; the host
+ * array may be freed on return.  Synchronous.  Errors: HX_ERR_ARG (n_g < 2,
+ * d_inv_g <= 0, non-finite entries), HX_ERR_OOM, HX_ERR_CUDA. */
+int hx_set_table(hx_ctx* ctx, const double* table_host, int n_g, double d_inv_g);
+
+/* ---------------------------------------------------------------- operator */
+
+/* y = A x for nrhs right-hand sides, A the impedance matrix [M + S] of Eq. 3
+ * built on the fly per row (Eqs. 4-8 with the GA weight selection): the row's
+ * 1/G = f h / v is looked up in the table by linear interpolation (clamped to
+ * the table), the stiffness is sum_d T_d[delta_d p] (stretched second
+ * differences averaged over the transverse 3x3 plane with weights
+ * ws1 + 2ws2/3 + ws3/2, ws2/12, ws3/8) and the mass is the second form of
+ * Eq. 8 with kappa at the collocation point.  shift_beta != 0 replaces
+ * omega^2 by (1 + i shift_beta) omega^2 (the complex-shifted operator of the
+ * preconditioner; 0 gives the paper's operator).
+ *   precision 32: x, y complex64, arithmetic FP32 (table in FP32);
+ *   precision 64: x, y complex128, arithmetic FP64.
+ *   x_dev, y_dev: [nrhs][nz][ny][nx], must not overlap.
+ * Velocities are not validated here (see hx_solve).  Asynchronous on stream.
+ * Errors: HX_ERR_ARG, HX_ERR_STATE (no table), HX_ERR_CUDA. */
+int hx_apply_operator(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
+                      double shift_beta, const void* x_dev, void* y_dev,
+                      int nrhs, int precision, void* stream);
+
+/* The 27 complex128 coefficients of every row of A (same definition as
+ * hx_apply_operator, FP64), written to coef_dev as [N][27][2] doubles in
+ * offset order (dk, dj, di) with each of dk, dj, di running -1, 0, 1
+ * (di fastest).  Entries whose neighbour lies outside the grid are written as
+ * 0.  For tests and for users who assemble the matrix themselves.  Async. */
+int hx_row_coefficients(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
+                        double shift_beta, double* coef_dev, void* stream);
+
+/* Assemble A as CSR on the host (complex128, lexicographic rows, columns
+ * sorted, entries outside the grid omitted).  Caller-owned host arrays:
+ * rowptr [N+1], col [nnz_cap], val [2*nnz_cap] (interleaved re, im);
+ * nnz_cap >= 27 N always suffices.  v_dev is on the device; the call
+ * synchronises `stream`.  Errors: HX_ERR_ARG (nnz_cap too small), others as
+ * above. */
+int hx_assemble_csr(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
+                    double shift_beta, int64_t* rowptr, int32_t* col,
+                    double* val, int64_t nnz_cap, int64_t* nnz_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HX27_H */

@@ -1,0 +1,184 @@
+"""ctypes binding of libhx27 (include/hx27.h): argument marshalling only.
+
+Device buffers are torch CUDA tensors (complex64 / complex128 / float32),
+passed by data_ptr() with the current torch stream.  Every compute step runs
+in the library's CUDA kernels; there is no Python or CPU fallback, and
+``lib()`` raises if the shared library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhx27.so")
+
+HX_OK = 0
+STATUS = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_OOM", -3: "HX_ERR_NOT_CONVERGED",
+          -4: "HX_ERR_NUMERIC", -5: "HX_ERR_TIMEOUT", -6: "HX_ERR_CUDA", -7: "HX_ERR_STATE"}
+
+# every symbol include/hx27.h declares (checked by tests/test_abi.py)
+EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_error",
+           "hx_set_table", "hx_apply_operator", "hx_row_coefficients", "hx_assemble_csr")
+
+
+class HxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class hx_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("h", C.c_double),
+                ("f", C.c_double), ("npml", C.c_int * 6), ("v_ref", C.c_double),
+                ("r_coef", C.c_double)]
+
+
+class hx_source(C.Structure):
+    _fields_ = [("ix", C.c_int), ("iy", C.c_int), ("iz", C.c_int), ("rhs", C.c_int),
+                ("amp_re", C.c_double), ("amp_im", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libhx27.so (built by ``paper_2108_08730_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2108_08730_gb300.build` (no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    vp, i, d, dp = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double)
+    L.hx_build_weight_table.argtypes = [dp, i, dp, i, d, d, d, dp, i, C.POINTER(C.c_int)]
+    L.hx_ctx_create.argtypes = [C.POINTER(vp), i]
+    L.hx_ctx_destroy.argtypes = [vp]
+    L.hx_ctx_destroy.restype = None
+    L.hx_last_error.argtypes = [vp]
+    L.hx_last_error.restype = C.c_char_p
+    L.hx_set_table.argtypes = [vp, dp, i, d]
+    L.hx_apply_operator.argtypes = [vp, C.POINTER(hx_grid), vp, d, vp, vp, i, i, vp]
+    L.hx_row_coefficients.argtypes = [vp, C.POINTER(hx_grid), vp, d, vp, vp]
+    L.hx_assemble_csr.argtypes = [vp, C.POINTER(hx_grid), vp, d, C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int32), dp, C.c_int64, C.POINTER(C.c_int64), vp]
+    for name in EXPORTS:
+        fn = getattr(L, name)
+        if name not in ("hx_ctx_destroy", "hx_last_error"):
+            fn.restype = C.c_int
+    _lib = L
+    return L
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def build_weight_table(theta_deg=(0, 10, 20, 30, 40, 45), phi_deg=(0, 10, 20, 30, 40, 45),
+                       inv_g_max=0.4, d_inv_g=0.001, lam=1e-6):
+    """hx_build_weight_table -> (inv_g nodes, table [n_g, 7]) as numpy FP64."""
+    L = lib()
+    th = np.ascontiguousarray(theta_deg, dtype=np.float64)
+    ph = np.ascontiguousarray(phi_deg, dtype=np.float64)
+    n_g = C.c_int(0)
+    cap = 7 * (int(round(inv_g_max / d_inv_g)) + 1)
+    out = np.zeros(cap, dtype=np.float64)
+    st = L.hx_build_weight_table(_dptr(th), th.size, _dptr(ph), ph.size, inv_g_max, d_inv_g, lam,
+                                 _dptr(out), cap, C.byref(n_g))
+    if st != HX_OK:
+        raise HxError(st, "hx_build_weight_table failed")
+    T = out[:7 * n_g.value].reshape(n_g.value, 7)
+    return np.arange(n_g.value) * d_inv_g, T
+
+
+def make_grid(shape, h, f, npml, v_ref, r_coef=1e-3):
+    """hx_grid from (nz, ny, nx) and the rest."""
+    nz, ny, nx = shape
+    g = hx_grid()
+    g.nx, g.ny, g.nz = int(nx), int(ny), int(nz)
+    g.h, g.f = float(h), float(f)
+    for k in range(6):
+        g.npml[k] = int(npml[k])
+    g.v_ref, g.r_coef = float(v_ref), float(r_coef)
+    return g
+
+
+def grid_of(workload):
+    return make_grid(workload.shape, workload.h, workload.f, workload.npml, workload.v_ref,
+                     workload.r_coef)
+
+
+def _stream_ptr(stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """Owns an hx_ctx on one CUDA device."""
+
+    def __init__(self, device=0, table=None, d_inv_g=0.001):
+        L = lib()
+        h = C.c_void_p()
+        st = L.hx_ctx_create(C.byref(h), int(device))
+        if st != HX_OK:
+            raise HxError(st, f"hx_ctx_create(device={device}) failed")
+        self._h = h
+        self.device = device
+        if table is not None:
+            self.set_table(table, d_inv_g)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hx_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != HX_OK:
+            msg = lib().hx_last_error(self._h)
+            raise HxError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def set_table(self, table, d_inv_g=0.001):
+        T = np.ascontiguousarray(table, dtype=np.float64)
+        self._check(lib().hx_set_table(self._h, _dptr(T), T.shape[0], float(d_inv_g)), "hx_set_table")
+
+    def apply(self, grid, v, x, y, shift_beta=0.0, stream=None):
+        """y = A x; v float32 (nz,ny,nx) and x, y complex64/complex128
+        (nrhs, nz, ny, nx) torch CUDA tensors."""
+        import torch
+        prec = 32 if x.dtype == torch.complex64 else 64
+        nrhs = x.shape[0] if x.dim() == 4 else 1
+        self._check(lib().hx_apply_operator(self._h, C.byref(grid), C.c_void_p(v.data_ptr()),
+                                            float(shift_beta), C.c_void_p(x.data_ptr()),
+                                            C.c_void_p(y.data_ptr()), nrhs, prec, _stream_ptr(stream)),
+                    "hx_apply_operator")
+
+    def row_coefficients(self, grid, v, coef, shift_beta=0.0, stream=None):
+        self._check(lib().hx_row_coefficients(self._h, C.byref(grid), C.c_void_p(v.data_ptr()),
+                                              float(shift_beta), C.c_void_p(coef.data_ptr()),
+                                              _stream_ptr(stream)), "hx_row_coefficients")
+
+    def assemble_csr(self, grid, v, shift_beta=0.0, stream=None):
+        """-> (rowptr int64, col int32, val complex128) numpy arrays."""
+        N = grid.nx * grid.ny * grid.nz
+        cap = 27 * N
+        rowptr = np.zeros(N + 1, dtype=np.int64)
+        col = np.zeros(cap, dtype=np.int32)
+        val = np.zeros(2 * cap, dtype=np.float64)
+        nnz = C.c_int64(0)
+        self._check(lib().hx_assemble_csr(
+            self._h, C.byref(grid), C.c_void_p(v.data_ptr()), float(shift_beta),
+            rowptr.ctypes.data_as(C.POINTER(C.c_int64)), col.ctypes.data_as(C.POINTER(C.c_int32)),
+            _dptr(val), cap, C.byref(nnz), _stream_ptr(stream)), "hx_assemble_csr")
+        n = nnz.value
+        return rowptr, col[:n].copy(), val[:2 * n].view(np.complex128).copy()

@@ -1,0 +1,329 @@
+// C-ABI entry points: context, weight table, operator apply / coefficients.
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hx_context.h"
+#include "hx_internal.h"
+
+namespace hx {
+
+Profile1D Profile1D::from_grid(int n, double h, int npml_lo, int npml_hi, double v_ref,
+                               double r_coef) {
+  auto g0 = [&](int np) { return np <= 0 ? 0.0 : 3.0 * v_ref / (2.0 * np * h) * std::log(1.0 / r_coef); };
+  return Profile1D{npml_lo * h, (n - 1 - npml_hi) * h, npml_lo * h, npml_hi * h, g0(npml_lo),
+                   g0(npml_hi)};
+}
+
+double Profile1D::gamma(double x) const {
+  double g = 0.0;
+  if (len_lo > 0) {
+    const double d = x_lo - x > 0 ? x_lo - x : 0.0;
+    g += g0_lo * (d / len_lo) * (d / len_lo);
+  }
+  if (len_hi > 0) {
+    const double d = x - x_hi > 0 ? x - x_hi : 0.0;
+    g += g0_hi * (d / len_hi) * (d / len_hi);
+  }
+  return g;
+}
+
+Level::~Level() {
+  for (int d = 0; d < 3; ++d) {
+    if (ax64[d]) cudaFree(ax64[d]);
+    if (ax32[d]) cudaFree(ax32[d]);
+  }
+}
+
+int fail(hx_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(hx_ctx* ctx, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(ctx, e == cudaErrorMemoryAllocation ? HX_ERR_OOM : HX_ERR_CUDA, m);
+}
+
+int check_grid(hx_ctx* ctx, const hx_grid* g) {
+  if (!g) return fail(ctx, HX_ERR_ARG, "grid is NULL");
+  const int n[3] = {g->nx, g->ny, g->nz};
+  for (int d = 0; d < 3; ++d) {
+    if (n[d] < 3) return fail(ctx, HX_ERR_ARG, "each grid dimension must be >= 3");
+    const int lo = g->npml[2 * d], hi = g->npml[2 * d + 1];
+    if (lo < 0 || hi < 0 || 2 * lo >= n[d] || 2 * hi >= n[d])
+      return fail(ctx, HX_ERR_ARG, "npml must satisfy 0 <= npml < n/2 on every face");
+  }
+  if ((double)g->nx * g->ny * g->nz > 4.0e9) return fail(ctx, HX_ERR_ARG, "grid too large");
+  if (!(g->h > 0) || !std::isfinite(g->h)) return fail(ctx, HX_ERR_ARG, "h must be > 0");
+  if (!(g->f > 0) || !std::isfinite(g->f)) return fail(ctx, HX_ERR_ARG, "f must be > 0");
+  if (!(g->v_ref > 0) || !std::isfinite(g->v_ref)) return fail(ctx, HX_ERR_ARG, "v_ref must be > 0");
+  if (!(g->r_coef > 0 && g->r_coef < 1)) return fail(ctx, HX_ERR_ARG, "r_coef must be in (0, 1)");
+  return HX_OK;
+}
+
+int get_level(hx_ctx* ctx, const hx_grid* g, const int nl[3], double hl, Level** out) {
+  char key[512];
+  std::snprintf(key, sizeof(key), "%d %d %d %.17g %.17g %d %d %d %d %d %d %.17g %.17g | %d %d %d %.17g",
+                g->nx, g->ny, g->nz, g->h, g->f, g->npml[0], g->npml[1], g->npml[2], g->npml[3],
+                g->npml[4], g->npml[5], g->v_ref, g->r_coef, nl[0], nl[1], nl[2], hl);
+  auto it = ctx->levels.find(key);
+  if (it != ctx->levels.end()) {
+    ctx->lru.remove(key);
+    ctx->lru.push_front(key);
+    *out = it->second.get();
+    return HX_OK;
+  }
+  while (ctx->levels.size() >= 64) {
+    ctx->levels.erase(ctx->lru.back());
+    ctx->lru.pop_back();
+  }
+  auto lv = std::make_unique<Level>();
+  const int nf[3] = {g->nx, g->ny, g->nz};
+  const double omega = 2.0 * M_PI * g->f;
+  lv->h = hl;
+  lv->f = g->f;
+  for (int d = 0; d < 3; ++d) {
+    lv->n[d] = nl[d];
+    const Profile1D prof =
+        Profile1D::from_grid(nf[d], g->h, g->npml[2 * d], g->npml[2 * d + 1], g->v_ref, g->r_coef);
+    std::vector<double> a64(4 * (size_t)nl[d]);
+    std::vector<float> a32(4 * (size_t)nl[d]);
+    const double ih2 = 1.0 / (hl * hl);
+    int lo = -1, hi = -2;
+    for (int i = 0; i < nl[d]; ++i) {
+      // xi = 1 + i gamma / omega at the node and the two half nodes
+      auto xi = [&](double x) { return std::complex<double>(1.0, prof.gamma(x) / omega); };
+      const std::complex<double> xn = xi(i * hl), xp = xi((i + 0.5) * hl), xm = xi((i - 0.5) * hl);
+      const std::complex<double> up = 1.0 / (xn * xp) * ih2, dn = 1.0 / (xn * xm) * ih2;
+      a64[4 * i + 0] = up.real();
+      a64[4 * i + 1] = up.imag();
+      a64[4 * i + 2] = dn.real();
+      a64[4 * i + 3] = dn.imag();
+      for (int k = 0; k < 4; ++k) a32[4 * i + k] = (float)a64[4 * i + k];
+      const bool plain = up.imag() == 0.0 && dn.imag() == 0.0 && up.real() == ih2 && dn.real() == ih2;
+      if (plain) {
+        if (lo < 0) lo = i;
+        hi = i;
+      }
+    }
+    // the plain nodes must be contiguous for the range test in the kernels
+    for (int i = (lo < 0 ? 0 : lo); i <= hi; ++i) {
+      if (!(a64[4 * i + 1] == 0.0 && a64[4 * i + 3] == 0.0)) return fail(ctx, HX_ERR_ARG, "PML layout");
+    }
+    lv->lo[d] = lo < 0 ? 1 : lo;
+    lv->hi[d] = lo < 0 ? 0 : hi;
+    cudaError_t e = cudaMalloc(&lv->ax64[d], a64.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&lv->ax32[d], a32.size() * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(lv->ax64[d], a64.data(), a64.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(lv->ax32[d], a32.data(), a32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "PML coefficient upload");
+  }
+  *out = lv.get();
+  ctx->levels[key] = std::move(lv);
+  ctx->lru.push_front(key);
+  return HX_OK;
+}
+
+template <typename T>
+OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double beta) {
+  OpDesc<T> d;
+  d.nx = lv.n[0];
+  d.ny = lv.n[1];
+  d.nz = lv.n[2];
+  d.v = v;
+  d.tab = sizeof(T) == 8 ? (const T*)ctx->tab64 : (const T*)ctx->tab32;
+  d.n_g = ctx->n_g;
+  d.u_scale = (T)(lv.f * lv.h / ctx->d_inv_g);
+  d.omega2 = (T)((2.0 * M_PI * lv.f) * (2.0 * M_PI * lv.f));
+  d.beta = (T)beta;
+  d.inv_h2 = (T)(1.0 / (lv.h * lv.h));
+  for (int a = 0; a < 3; ++a) {
+    d.axis[a] = sizeof(T) == 8 ? (const T*)lv.ax64[a] : (const T*)lv.ax32[a];
+    d.plain_lo[a] = lv.lo[a];
+    d.plain_hi[a] = lv.hi[a];
+  }
+  return d;
+}
+
+template OpDesc<float> make_desc<float>(const hx_ctx*, const Level&, const float*, double);
+template OpDesc<double> make_desc<double>(const hx_ctx*, const Level&, const float*, double);
+
+}  // namespace hx
+
+hx_ctx::~hx_ctx() {
+  solvers.clear();
+  levels.clear();
+  if (tab64) cudaFree(tab64);
+  if (tab32) cudaFree(tab32);
+}
+
+using namespace hx;
+
+extern "C" {
+
+int hx_build_weight_table(const double* theta_deg, int n_theta, const double* phi_deg, int n_phi,
+                          double inv_g_max, double d_inv_g, double lambda, double* table_out,
+                          int capacity, int* n_g_out) {
+  std::string err;
+  return build_weight_table(theta_deg, n_theta, phi_deg, n_phi, inv_g_max, d_inv_g, lambda,
+                            table_out, capacity, n_g_out, &err);
+}
+
+int hx_ctx_create(hx_ctx** out, int device) {
+  if (!out) return HX_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return HX_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return HX_ERR_CUDA;
+  hx_ctx* c = new (std::nothrow) hx_ctx();
+  if (!c) return HX_ERR_OOM;
+  c->device = device;
+  *out = c;
+  return HX_OK;
+}
+
+void hx_ctx_destroy(hx_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  delete ctx;
+}
+
+const char* hx_last_error(const hx_ctx* ctx) {
+  if (!ctx) return "no context";
+  return ctx->err.c_str();
+}
+
+int hx_set_table(hx_ctx* ctx, const double* table, int n_g, double d_inv_g) {
+  if (!ctx) return HX_ERR_ARG;
+  if (!table || n_g < 2 || !(d_inv_g > 0)) return fail(ctx, HX_ERR_ARG, "need table, n_g >= 2, d_inv_g > 0");
+  for (int i = 0; i < 7 * n_g; ++i)
+    if (!std::isfinite(table[i])) return fail(ctx, HX_ERR_ARG, "table has non-finite entries");
+  cudaSetDevice(ctx->device);
+  std::vector<double> d64((size_t)n_g * kTabW, 0.0);
+  std::vector<float> d32((size_t)n_g * kTabW, 0.f);
+  for (int i = 0; i < n_g; ++i) {
+    const double* w = table + 7 * (size_t)i;
+    const double ws2 = w[1], ws3 = w[2];
+    const double t0 = w[0] + 2.0 * ws2 / 3.0 + 0.5 * ws3;
+    double* o = &d64[(size_t)i * kTabW];
+    o[0] = -6.0 * t0;
+    o[1] = t0 - ws2 / 3.0;
+    o[2] = ws2 / 6.0 - ws3 / 4.0;
+    o[3] = 3.0 * ws3 / 8.0;
+    for (int k = 0; k < 4; ++k) o[4 + k] = w[3 + k];
+    o[8] = t0;
+    o[9] = ws2 / 12.0;
+    o[10] = ws3 / 8.0;
+    for (int k = 0; k < kTabW; ++k) d32[(size_t)i * kTabW + k] = (float)o[k];
+  }
+  if (ctx->tab64) cudaFree(ctx->tab64);
+  if (ctx->tab32) cudaFree(ctx->tab32);
+  ctx->tab64 = nullptr;
+  ctx->tab32 = nullptr;
+  cudaError_t e = cudaMalloc(&ctx->tab64, d64.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->tab32, d32.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->tab64, d64.data(), d64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->tab32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "table upload");
+  ctx->table.assign(table, table + 7 * (size_t)n_g);
+  ctx->n_g = n_g;
+  ctx->d_inv_g = d_inv_g;
+  ctx->solvers.clear();
+  ctx->solver_lru.clear();
+  return HX_OK;
+}
+
+int hx_apply_operator(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, double shift_beta,
+                      const void* x_dev, void* y_dev, int nrhs, int precision, void* stream) {
+  if (!ctx) return HX_ERR_ARG;
+  int st = check_grid(ctx, grid);
+  if (st) return st;
+  if (!ctx->tab64) return fail(ctx, HX_ERR_STATE, "no weight table set (hx_set_table)");
+  if (!v_dev || !x_dev || !y_dev || nrhs < 1) return fail(ctx, HX_ERR_ARG, "null buffer or nrhs < 1");
+  if (x_dev == y_dev) return fail(ctx, HX_ERR_ARG, "x and y must not overlap");
+  if (precision != 32 && precision != 64) return fail(ctx, HX_ERR_ARG, "precision must be 32 or 64");
+  if (!std::isfinite(shift_beta)) return fail(ctx, HX_ERR_ARG, "shift_beta must be finite");
+  cudaSetDevice(ctx->device);
+  Level* lv = nullptr;
+  const int nl[3] = {grid->nx, grid->ny, grid->nz};
+  if ((st = get_level(ctx, grid, nl, grid->h, &lv))) return st;
+  const long long N = (long long)grid->nx * grid->ny * grid->nz;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (precision == 32)
+    e = launch_stencil(make_desc<float>(ctx, *lv, v_dev, shift_beta), kApply, x_dev, nullptr, y_dev, nrhs, N, 0.0, s);
+  else
+    e = launch_stencil(make_desc<double>(ctx, *lv, v_dev, shift_beta), kApply, x_dev, nullptr, y_dev, nrhs, N, 0.0, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "apply launch");
+  return HX_OK;
+}
+
+int hx_row_coefficients(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, double shift_beta,
+                        double* coef_dev, void* stream) {
+  if (!ctx) return HX_ERR_ARG;
+  int st = check_grid(ctx, grid);
+  if (st) return st;
+  if (!ctx->tab64) return fail(ctx, HX_ERR_STATE, "no weight table set (hx_set_table)");
+  if (!v_dev || !coef_dev) return fail(ctx, HX_ERR_ARG, "null buffer");
+  cudaSetDevice(ctx->device);
+  Level* lv = nullptr;
+  const int nl[3] = {grid->nx, grid->ny, grid->nz};
+  if ((st = get_level(ctx, grid, nl, grid->h, &lv))) return st;
+  cudaError_t e = launch_row_coefficients(make_desc<double>(ctx, *lv, v_dev, shift_beta), coef_dev,
+                                          (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "row coefficient launch");
+  return HX_OK;
+}
+
+int hx_assemble_csr(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, double shift_beta,
+                    int64_t* rowptr, int32_t* col, double* val, int64_t nnz_cap, int64_t* nnz_out,
+                    void* stream) {
+  if (!ctx) return HX_ERR_ARG;
+  int st = check_grid(ctx, grid);
+  if (st) return st;
+  if (!rowptr || !col || !val || !nnz_out) return fail(ctx, HX_ERR_ARG, "null host buffer");
+  const long long N = (long long)grid->nx * grid->ny * grid->nz;
+  if (N > (1LL << 31) / 27) return fail(ctx, HX_ERR_ARG, "grid too large for 32-bit CSR columns");
+  cudaSetDevice(ctx->device);
+  double* coef = nullptr;
+  cudaError_t e = cudaMalloc(&coef, (size_t)N * 27 * 2 * sizeof(double));
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "coefficient buffer");
+  st = hx_row_coefficients(ctx, grid, v_dev, shift_beta, coef, stream);
+  std::vector<double> h;
+  if (!st) {
+    h.resize((size_t)N * 54);
+    e = cudaMemcpyAsync(h.data(), coef, h.size() * sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "coefficient download");
+  }
+  cudaFree(coef);
+  if (st) return st;
+  const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+  int64_t nnz = 0;
+  rowptr[0] = 0;
+  for (long long i = 0; i < N; ++i) {
+    const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((long long)nx * ny));
+    int k = 0;
+    for (int dk = -1; dk <= 1; ++dk)
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di, ++k) {
+          if (ix + di < 0 || ix + di >= nx || iy + dj < 0 || iy + dj >= ny || iz + dk < 0 || iz + dk >= nz)
+            continue;
+          if (nnz >= nnz_cap) return fail(ctx, HX_ERR_ARG, "nnz_cap too small");
+          col[nnz] = (int32_t)(i + di + (long long)nx * (dj + (long long)ny * dk));
+          val[2 * nnz] = h[(size_t)i * 54 + 2 * k];
+          val[2 * nnz + 1] = h[(size_t)i * 54 + 2 * k + 1];
+          ++nnz;
+        }
+    rowptr[i + 1] = nnz;
+  }
+  *nnz_out = nnz;
+  return HX_OK;
+}
+
+}  // extern "C"

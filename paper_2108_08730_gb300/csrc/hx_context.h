@@ -1,0 +1,70 @@
+// Context object behind the opaque hx_ctx handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <list>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "hx_internal.h"
+
+namespace hx {
+
+// Physical PML profile of one axis (the reading documented in hx27.h).
+struct Profile1D {
+  double x_lo, x_hi, len_lo, len_hi, g0_lo, g0_hi;
+  static Profile1D from_grid(int n, double h, int npml_lo, int npml_hi, double v_ref,
+                             double r_coef);
+  double gamma(double x) const;
+};
+
+// Operator data of one grid level: per-axis PML coefficients on the device.
+struct Level {
+  int n[3] = {0, 0, 0};
+  double h = 0, f = 0;
+  double* ax64[3] = {nullptr, nullptr, nullptr};
+  float* ax32[3] = {nullptr, nullptr, nullptr};
+  int lo[3] = {0, 0, 0}, hi[3] = {-1, -1, -1};
+  ~Level();
+};
+
+// Solver workspaces (defined by the solver translation unit).
+struct Solver {
+  virtual ~Solver() = default;
+};
+
+}  // namespace hx
+
+struct hx_ctx {
+  int device = 0;
+  std::string err;
+  // weight table
+  int n_g = 0;
+  double d_inv_g = 0;
+  std::vector<double> table;    // host copy [n_g][7]
+  double* tab64 = nullptr;      // derived [n_g][kTabW]
+  float* tab32 = nullptr;
+  // cached levels, keyed by their defining parameters
+  std::map<std::string, std::unique_ptr<hx::Level>> levels;
+  std::list<std::string> lru;
+  std::map<std::string, std::unique_ptr<hx::Solver>> solvers;
+  std::list<std::string> solver_lru;
+
+  ~hx_ctx();
+};
+
+namespace hx {
+
+int fail(hx_ctx* ctx, int code, const std::string& msg);
+int cuda_fail(hx_ctx* ctx, cudaError_t e, const char* where);
+int check_grid(hx_ctx* ctx, const hx_grid* g);
+// Level for grid g evaluated at spacing h_level with n_level nodes per axis
+// (level 0: the grid itself).  Returned pointer is owned by ctx.
+int get_level(hx_ctx* ctx, const hx_grid* g, const int n_level[3], double h_level, Level** out);
+template <typename T>
+OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double beta);
+
+}  // namespace hx

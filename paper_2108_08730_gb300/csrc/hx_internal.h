@@ -1,0 +1,52 @@
+// Internal declarations shared by the translation units of libhx27.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/hx27.h"
+
+namespace hx {
+
+// Derived per-table-node quantities (all linear in the 7 weights, so
+// interpolating them equals deriving them from the interpolated weights):
+//   0..3  stiffness class coefficients times h^2 of an interior row
+//         (centre, face, edge, corner): -6 t0, t0 - ws2/3, ws2/6 - ws3/4, 3 ws3/8
+//   4..7  per-point mass weights wm1..wm4
+//   8..10 transverse-average weights t0 = ws1 + 2ws2/3 + ws3/2, t1 = ws2/12,
+//         t2 = ws3/8 of the stiffness  S = sum_d T_d[delta_d p]
+constexpr int kTabW = 12;
+
+int build_weight_table(const double* theta_deg, int n_theta, const double* phi_deg, int n_phi,
+                       double inv_g_max, double d_inv_g, double lambda, double* out, int capacity,
+                       int* n_g_out, std::string* err);
+
+// Per-level operator description handed to the kernels (device pointers).
+template <typename T>
+struct OpDesc {
+  int nx, ny, nz;
+  const float* v;          // velocity [nz][ny][nx]
+  const T* tab;            // [n_g][kTabW]
+  int n_g;
+  T u_scale;               // f h / d_inv_g  ->  table coordinate u = u_scale / v
+  T omega2;                // omega^2
+  T beta;                  // CSL shift
+  T inv_h2;                // 1 / h^2
+  const T* axis[3];        // per axis: [n][4] = (up.re, up.im, dn.re, dn.im)
+  int plain_lo[3], plain_hi[3];  // nodes whose up = dn = 1/h^2 exactly
+};
+
+enum StencilMode { kApply = 0, kResidual = 1, kJacobi = 2 };
+
+// Launch y = A x (kApply), y = b - A x (kResidual) or
+// y = x + omega_j D^{-1} (b - A x) (kJacobi) for nrhs fields of stride
+// `rstride` elements.  Returns a cudaError_t.
+template <typename T>
+cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const void* b, void* y,
+                           int nrhs, long long rstride, double omega_j, cudaStream_t s);
+
+cudaError_t launch_row_coefficients(const OpDesc<double>& op, double* coef, cudaStream_t s);
+
+}  // namespace hx

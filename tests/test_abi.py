@@ -1,0 +1,85 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol
+include/hx27.h declares, rejects bad arguments, and its host weight fit
+(Section 2.2, banded Givens QR) matches the oracle's SVD least squares."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2108_08730_gb300 import binding as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:int|void|const char\*)\s+(hx_\w+)\s*\(", src, re.M))
+    return names
+
+
+def test_header_declares_the_binding_exports():
+    assert _declared() == set(B.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    L = B.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+
+
+def test_weight_table_argument_errors():
+    L = B.lib()
+    th = np.zeros(3)
+    out = np.zeros(10)
+    n = C.c_int(0)
+    dp = C.POINTER(C.c_double)
+    st = L.hx_build_weight_table(th.ctypes.data_as(dp), 3, th.ctypes.data_as(dp), 3, 0.4, 0.001,
+                                 1e-6, out.ctypes.data_as(dp), 10, C.byref(n))
+    assert st == -1 and n.value == 401            # capacity too small, n_g reported
+    st = L.hx_build_weight_table(th.ctypes.data_as(dp), 3, th.ctypes.data_as(dp), 3, 0.4, 0.001,
+                                 0.0, out.ctypes.data_as(dp), 10, C.byref(n))
+    assert st == -1                               # lambda must be > 0
+    assert B.lib().hx_last_error(None) == b"no context"
+
+
+@pytest.fixture(scope="module")
+def tables():
+    from oracle import weights as W
+    return W.fit_table(), B.build_weight_table()
+
+
+def test_host_fit_matches_oracle(tables):
+    # Same regularised problem, different algorithms (oracle: dense SVD lstsq;
+    # library: banded Givens QR).  The stacked system's condition number is
+    # ~2.5e7 at lambda = 1e-6, so agreement to ~cond * eps (here 1e-8 on weights
+    # of size ~1) is what FP64 allows.
+    (nodes_o, To), (nodes_l, Tl) = tables
+    assert Tl.shape == To.shape == (401, 7)
+    assert np.allclose(nodes_o, nodes_l)
+    assert np.max(np.abs(Tl - To)) < 1e-8
+
+
+def test_host_fit_constraints_and_dispersion(tables):
+    from oracle import weights as W
+    _, (nodes, T) = tables
+    assert np.max(np.abs(T[:, :3].sum(1) - 1)) < 1e-14
+    assert np.max(np.abs(T[:, 3] + 6 * T[:, 4] + 12 * T[:, 5] + 8 * T[:, 6] - 1)) < 1e-14
+    th, ph = W.angle_grid()
+    for i in (25, 100, 250, 400):
+        w_opt, _ = W.fit_per_g(nodes[i])
+        e_opt = np.max(np.abs(W.phase_velocity(nodes[i], th, ph, W.expand_weights(w_opt)) - 1))
+        e = np.max(np.abs(W.phase_velocity(nodes[i], th, ph, T[i]) - 1))
+        assert e <= max(1.05 * e_opt, e_opt + 1e-6)
+
+
+def test_ctx_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("GPU present")
+    with pytest.raises(B.HxError):
+        B.Context(0)
