@@ -1,0 +1,423 @@
+"""Benchmark: Mpoint*RHS/s of the wavelength-adaptive 27-point Helmholtz solve.
+
+One step = one hx_solve (complex64 Krylov + CSL multigrid, FP64 iterative
+refinement to a relative FP64 residual of --tol) of the linear-gradient
+workload (101^3 grid incl. a 10-node PML, h = 20 m, f = 5 Hz, one source near
+the surface), sources on the device to the wavefield on the device.  L2 is
+flushed (512 MB write) between timed steps, outside the timed intervals.
+
+Also reported on the same JSON line:
+  e2e          same solve through the C ABI from pinned HOST buffers (velocity
+               up, wavefield down) with the copies inside the timed interval;
+  roofline     dominant fine-level kernel class: algorithmic bytes / CUDA-event
+               time of its launches inside the timed steps, against the measured
+               HBM copy bandwidth in MEASURED_PEAKS.json;
+  accuracy     relative L2 error of the mixed solution against the plain FP64
+               GPU solve, and that FP64 form's own throughput;
+  cpu_baseline the CPU oracle (banded LU, all host cores) on a bounded sample
+               of the same workload: the 24^3 corner-free sub-grid around the
+               source with the same model, PML and frequency.
+
+--impl reference runs the oracle alone (rank 0), on the same metric.
+Multi-GPU: one process per GPU (torchrun); every rank solves its own copy of
+the workload (independent problems, no collective on the data path); the value
+is all ranks' point*RHS over the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoint*RHS/s to 1e-6 rel err (mixed vs FP64 GPU)"
+UNIT = "Mpoint*RHS/s"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="hx", choices=["hx", "reference"])
+    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--kernel", action="store_true", help="time the operator apply alone")
+    p.add_argument("--kernel-workload", default="tectonic")
+    p.add_argument("--kernel-nrhs", type=int, default=4)
+    p.add_argument("--kernel-prec", type=int, default=32, choices=[32, 64])
+    return p.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------- oracle
+
+def _oracle_sample(n=24):
+    """Bounded CPU sample of the linear-gradient workload: an n^3 sub-grid of
+    the same model (same h, f, velocity law, PML thickness and source depth)."""
+    from paper_2108_08730_gb300 import synth
+    wl = synth.linear_gradient(n=n, npml=10 if n >= 30 else 6)
+    return wl
+
+
+def oracle_rate(budget_s=12.0, n=24):
+    """Time the oracle (assemble + banded LU) on the bounded sample; returns
+    (Mpoint*RHS/s, seconds, repeats, sample description, threads)."""
+    from oracle import operator as O
+    from oracle import solve as S
+    from oracle import weights as W
+    nodes, T = W.fit_table()
+    wl = _oracle_sample(n)
+    prof = O.profiles_for(wl.shape, wl.h, wl.npml, wl.v_ref, wl.r_coef)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        A = O.assemble_csr(wl.v, wl.h, wl.f, prof, T, nodes)
+        s = S.point_sources(wl.shape, wl.h, wl.sources)
+        S.solve_banded(A, s.reshape(-1))
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 50:
+            break
+    rate = wl.n_points * wl.nrhs * reps / el / 1e6
+    desc = (f"banded LU (scipy solve_banded, LAPACK gbsv) + CSR assembly of a {n}^3 sub-grid of the "
+            f"linear-gradient model (same h, f, v law, {wl.npml[0]}-node PML), {reps} solves")
+    return rate, el, reps, desc, os.cpu_count()
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    steps = []
+    for k in range(args.warmup + args.steps):
+        r, el, reps, desc, cores = oracle_rate(budget_s=4.0)
+        if k >= args.warmup:
+            steps.append((r, el / reps))
+    value = statistics.mean(s[0] for s in steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * statistics.mean(s[1] for s in steps), 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": "linear_gradient (bounded CPU sample)", "sample": desc},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_per_launch(kind):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel source changed since the capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path))
+        src = os.path.join(ROOT, "paper_2108_08730_gb300", "csrc", "hx_stencil.cu")
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if rec.get("source_sha") != h:
+            return None
+        return rec.get(kind, {}).get("bytes_per_launch_full_size")
+    except Exception:
+        return None
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2108_08730_gb300 import binding as B
+    from paper_2108_08730_gb300 import synth
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+
+    nodes, T = B.build_weight_table()
+    ctx = B.Context(local, table=T)
+    wl = synth.linear_gradient()
+    g = B.grid_of(wl)
+    src = B.sources_of(wl)
+    R = wl.nrhs
+    N = wl.n_points
+    units = N * R
+    v_host = torch.from_numpy(wl.v).pin_memory()
+    vd = v_host.to(dev)
+    out = torch.zeros((R,) + wl.shape, dtype=torch.complex128, device=dev)
+    out_host = torch.empty((R,) + wl.shape, dtype=torch.complex128).pin_memory()
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = dict(tol=args.tol)
+
+    def solve():
+        return ctx.solve(g, vd, src, R, out, **opts)
+
+    for _ in range(max(args.warmup, 0)):
+        solve()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed steps (+ live per-kernel timing)
+    clocks = Clocks(local)
+    ctx.profile(True)
+    barrier()
+    clocks.start()
+    step_ms, reports = [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rep = solve()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        reports.append(rep)
+    barrier()
+    clk = clocks.stop()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = units * world * args.steps / (total_ms / 1e3) / 1e6
+
+    # ---- end to end through the C ABI from pinned host buffers
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 3))):
+        flush.fill_(1.0)
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        vd.copy_(v_host, non_blocking=True)
+        solve()
+        out_host.copy_(out, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = units * world * len(e2e_ms) / (e2e_total / 1e3) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- accuracy against the plain FP64 GPU form (and its throughput)
+    acc = {}
+    if not args.no_fp64:
+        mixed = out.clone()
+        ref = torch.zeros_like(out)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep64 = ctx.solve(g, vd, src, R, ref, mode=B.SOLVE_FP64, tol=1e-12, max_iter=20000, check=False)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        err = float(torch.linalg.vector_norm(mixed - ref) / torch.linalg.vector_norm(ref))
+        acc = {"rel_l2_mixed_vs_fp64": err, "fp64_status": rep64["status"],
+               "fp64_rel_residual": rep64["rel_residual"], "fp64_iters": rep64["inner_iters"],
+               "fp64_value": round(units / t64 / 1e6, 4), "fp64_unit": UNIT,
+               "speedup_mixed_vs_fp64": round(value / world / (units / t64 / 1e6), 2)}
+
+    # ---- roofline of the dominant kernel class
+    peaks = _peaks()
+    kinds = {k: v for k, v in prof.items() if k != "all" and v[0] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][1]) if kinds else None
+    roof = None
+    if dom:
+        n, ms, by = kinds[dom]
+        achieved = by / (ms / 1e3) / 1e9
+        peak = peaks["hbm_gbs"] if peaks else 6800.0
+        tr = _traffic_per_launch(dom)
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": tr,
+                "kernel": {"apply32": "stencil_kernel<float, kApply>",
+                           "smooth32": "stencil_kernel<float, kJacobi|kResidual>",
+                           "apply64": "stencil_kernel<double, ...>",
+                           "smooth64": "stencil_kernel<double, kJacobi|kResidual>"}[dom],
+                "launches": n, "algo_bytes_per_launch": by / n,
+                "share_of_step": round(ms / total_ms, 4),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"}
+
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        r, el, reps, desc, cores = oracle_rate()
+        cpu = {"value": round(r, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    rep = reports[-1]
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 (Krylov+multigrid) + f64 (residual/refinement)", "data": "synthetic",
+        "config": {"workload": "linear_gradient: v=1500+0.7z, 101^3 incl. 10-node PML, h=20 m, f=5 Hz, "
+                               "1 source at (50,50,13)", "nrhs": R, "points": N, "tol": args.tol,
+                   "l2": "flushed between steps (512 MB write, outside the timed intervals)",
+                   "parallelism": f"replicas x{world}"},
+        "solve": {"outer_iters": rep["outer_iters"], "inner_iters": rep["inner_iters"],
+                  "mg_levels": rep["mg_levels"], "rel_residual": rep["rel_residual"]},
+        "accuracy": acc,
+        "e2e": {"value": round(e2e_value, 4), "unit": UNIT,
+                "h2d_bytes_per_step": int(v_host.numel() * 4),
+                "d2h_bytes_per_step": int(out_host.numel() * 16)},
+        "roofline": roof,
+        "gpu_launches": int(prof["all"][0]),
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_kernel(args):
+    """Time hx_apply_operator alone (complex64 or complex128) on a full-size
+    model: --kernel-workload (tectonic 401x401x187 by default) with
+    --kernel-nrhs right-hand sides; L2 flushed before every timed launch."""
+    import torch
+
+    from paper_2108_08730_gb300 import binding as B
+    from paper_2108_08730_gb300 import synth
+
+    nodes, T = B.build_weight_table()
+    ctx = B.Context(0, table=T)
+    wl = synth.CONFIGS[args.kernel_workload]()
+    g = B.grid_of(wl)
+    vd = torch.from_numpy(wl.v).cuda()
+    R = args.kernel_nrhs
+    dt = torch.complex64 if args.kernel_prec == 32 else torch.complex128
+    x = torch.randn((R,) + wl.shape, dtype=dt, device="cuda")
+    y = torch.empty_like(x)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.apply(g, vd, x, y)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        ctx.apply(g, vd, x, y)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    cb = 8 if args.kernel_prec == 32 else 16
+    algo = 2 * cb * wl.n_points * R + 4 * wl.n_points
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    print(json.dumps({"kernel": f"hx_apply_operator fp{args.kernel_prec}", "workload": wl.name,
+                      "nrhs": R, "points": wl.n_points, "ms": round(ms, 4),
+                      "Gpoint_rhs_per_s": round(wl.n_points * R / ms / 1e6, 3),
+                      "algo_bytes": algo, "achieved_gbs": round(algo / ms / 1e6, 1),
+                      "peak_gbs": peak, "frac": round(algo / ms / 1e6 / peak, 4)}), flush=True)
+
+
+def main():
+    args = _args()
+    if args.kernel:
+        run_kernel(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

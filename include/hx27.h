@@ -151,6 +151,91 @@ int hx_assemble_csr(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
                     double shift_beta, int64_t* rowptr, int32_t* col,
                     double* val, int64_t nnz_cap, int64_t* nnz_out, void* stream);
 
+/* ---------------------------------------------------------------- solve */
+
+enum { HX_SOLVE_MIXED = 0, HX_SOLVE_FP64 = 1 };
+
+/* Options of hx_solve (hx_solve_default_opts fills the defaults shown). */
+typedef struct {
+  int mode;              /* HX_SOLVE_MIXED (default): complex64 Krylov + multigrid
+                            inner solves inside FP64 iterative refinement;
+                            HX_SOLVE_FP64: the same Krylov + multigrid in FP64   */
+  double tol;            /* stop when every RHS has ||s - A x|| <= tol ||s||,
+                            residual computed in FP64 (default 1e-10)            */
+  double inner_tol;      /* relative residual reduction of each complex64 inner
+                            solve (mixed mode; default 1e-4)                    */
+  int max_outer;         /* refinement steps (default 12)                         */
+  int max_iter;          /* BiCGStab iterations per inner solve (default 2000)    */
+  double shift_beta;     /* complex shift of the preconditioner (default 0.5)    */
+  int mg_levels;         /* multigrid levels incl. the fine grid; 0 = automatic   */
+  int nu_pre, nu_post;   /* damped-Jacobi sweeps before / after coarse correction */
+  int coarse_sweeps;     /* damped-Jacobi sweeps on the coarsest level            */
+  double omega_jacobi;   /* Jacobi damping (default 0.7)                          */
+  int source_spread;     /* 0: grid delta (default); 1: consistent-mass spread    */
+  int initial_guess;     /* 1: wavefield_dev holds the starting iterate           */
+  int check_every;       /* iterations between host convergence checks (1)       */
+} hx_solve_opts;
+
+typedef struct {
+  int status;               /* same as the return value                          */
+  int outer_iters;          /* FP64 residual evaluations after the first          */
+  int inner_iters;          /* BiCGStab iterations summed over inner solves       */
+  int mg_levels;            /* levels used                                        */
+  double rel_residual;      /* max over RHS of ||s - A x|| / ||s|| (FP64)         */
+  double setup_ms, solve_ms;
+} hx_solve_report;
+
+void hx_solve_default_opts(hx_solve_opts* opts);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* Kernel classes timed by the profiler. */
+enum {
+  HX_PROF_APPLY32 = 0,   /* fine-level y = A x, complex64 (Krylov operator)      */
+  HX_PROF_SMOOTH32 = 1,  /* fine-level Jacobi / residual sweeps, complex64       */
+  HX_PROF_APPLY64 = 2,   /* fine-level FP64 operator (residual or Krylov)        */
+  HX_PROF_SMOOTH64 = 3,  /* fine-level Jacobi / residual sweeps, complex128      */
+  HX_PROF_KINDS = 4
+};
+
+/* Enable (1) or disable (0) per-launch timing of the fine-level operator
+ * kernels inside hx_solve and reset the counters.  When enabled, each such
+ * launch is bracketed by a CUDA event pair on the solve's stream and its
+ * duration, launch count and algorithmic bytes (x, b read + y written once,
+ * v read once: (8|16) * (2|3) * N * nrhs + 4 N) are accumulated; read them
+ * with hx_profile_read.  Also counts every kernel the library launches. */
+int hx_profile(hx_ctx* ctx, int enable);
+
+/* kind in [0, HX_PROF_KINDS): launches, summed duration (ms) and summed
+ * algorithmic bytes of that class since hx_profile(ctx, 1).  kind = -1:
+ * launches = all kernels launched by the library on this context (any
+ * class, also when timing is off), total_ms = bytes = 0. */
+int hx_profile_read(hx_ctx* ctx, int kind, int64_t* launches, double* total_ms,
+                    double* algo_bytes);
+
+/* Solve [M + S] p = s (Eq. 3) for nrhs right-hand sides built from point
+ * sources (Section 3.1), GA weights per row, with the given grid/PML.
+ * Method (not in the paper, which uses a sparse direct solver): BiCGStab
+ * right-preconditioned by a V-cycle of the complex-shifted operator
+ * (omega^2 -> (1 + i beta) omega^2) on grids coarsened by 2 (vertex-centred,
+ * velocity injected, same stencil and PML profile rediscretised at 2^l h,
+ * 1/G clamped to the table), damped-Jacobi smoothing, full-weighting
+ * restriction, trilinear prolongation.  Mixed mode runs that in complex64 and
+ * corrects an FP64 iterate with FP64 residuals until opts.tol.
+ *   v_dev: float32 [nz][ny][nx], every value finite, > 0 and with
+ *          f h / v <= the table's largest 1/G (HX_ERR_ARG otherwise).
+ *   src:   host array of nsrc sources; every rhs in [0, nrhs) must have one.
+ *   wavefield_dev: complex128 [nrhs][nz][ny][nx], receives p (and holds the
+ *          initial guess when opts->initial_guess).
+ *   opts:  NULL = defaults.  report: may be NULL.
+ * The ctx keeps the workspaces for the grid size and nrhs (reused by later
+ * calls).  Synchronises `stream` (convergence checks read norms on the host).
+ * Errors: HX_ERR_ARG, HX_ERR_STATE, HX_ERR_OOM, HX_ERR_CUDA, HX_ERR_NUMERIC
+ * (breakdown / non-finite residual), HX_ERR_NOT_CONVERGED (best iterate kept). */
+int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, const hx_source* src,
+             int nsrc, int nrhs, void* wavefield_dev, const hx_solve_opts* opts,
+             hx_solve_report* report, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

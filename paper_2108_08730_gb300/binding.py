@@ -21,7 +21,12 @@ STATUS = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_OOM", -3: "HX_ERR_NOT_CONVER
 
 # every symbol include/hx27.h declares (checked by tests/test_abi.py)
 EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_error",
-           "hx_set_table", "hx_apply_operator", "hx_row_coefficients", "hx_assemble_csr")
+           "hx_set_table", "hx_apply_operator", "hx_row_coefficients", "hx_assemble_csr",
+           "hx_solve_default_opts", "hx_solve", "hx_profile", "hx_profile_read")
+
+PROF_KINDS = {"apply32": 0, "smooth32": 1, "apply64": 2, "smooth64": 3}
+
+SOLVE_MIXED, SOLVE_FP64 = 0, 1
 
 
 class HxError(RuntimeError):
@@ -39,6 +44,23 @@ class hx_grid(C.Structure):
 class hx_source(C.Structure):
     _fields_ = [("ix", C.c_int), ("iy", C.c_int), ("iz", C.c_int), ("rhs", C.c_int),
                 ("amp_re", C.c_double), ("amp_im", C.c_double)]
+
+
+class hx_solve_opts(C.Structure):
+    _fields_ = [("mode", C.c_int), ("tol", C.c_double), ("inner_tol", C.c_double),
+                ("max_outer", C.c_int), ("max_iter", C.c_int), ("shift_beta", C.c_double),
+                ("mg_levels", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
+                ("coarse_sweeps", C.c_int), ("omega_jacobi", C.c_double),
+                ("source_spread", C.c_int), ("initial_guess", C.c_int), ("check_every", C.c_int)]
+
+
+class hx_solve_report(C.Structure):
+    _fields_ = [("status", C.c_int), ("outer_iters", C.c_int), ("inner_iters", C.c_int),
+                ("mg_levels", C.c_int), ("rel_residual", C.c_double), ("setup_ms", C.c_double),
+                ("solve_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -65,9 +87,15 @@ def lib():
     L.hx_row_coefficients.argtypes = [vp, C.POINTER(hx_grid), vp, d, vp, vp]
     L.hx_assemble_csr.argtypes = [vp, C.POINTER(hx_grid), vp, d, C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int32), dp, C.c_int64, C.POINTER(C.c_int64), vp]
+    L.hx_solve_default_opts.argtypes = [C.POINTER(hx_solve_opts)]
+    L.hx_solve_default_opts.restype = None
+    L.hx_solve.argtypes = [vp, C.POINTER(hx_grid), vp, C.POINTER(hx_source), i, i, vp,
+                           C.POINTER(hx_solve_opts), C.POINTER(hx_solve_report), vp]
+    L.hx_profile.argtypes = [vp, i]
+    L.hx_profile_read.argtypes = [vp, i, C.POINTER(C.c_int64), dp, dp]
     for name in EXPORTS:
         fn = getattr(L, name)
-        if name not in ("hx_ctx_destroy", "hx_last_error"):
+        if name not in ("hx_ctx_destroy", "hx_last_error", "hx_solve_default_opts"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -92,6 +120,23 @@ def build_weight_table(theta_deg=(0, 10, 20, 30, 40, 45), phi_deg=(0, 10, 20, 30
         raise HxError(st, "hx_build_weight_table failed")
     T = out[:7 * n_g.value].reshape(n_g.value, 7)
     return np.arange(n_g.value) * d_inv_g, T
+
+
+def default_opts(**kw):
+    """hx_solve_opts with the library defaults, overridden by keyword fields."""
+    o = hx_solve_opts()
+    lib().hx_solve_default_opts(C.byref(o))
+    names = {k for k, _ in hx_solve_opts._fields_}
+    for k, val in kw.items():
+        if k not in names:
+            raise KeyError(f"unknown solve option {k}")
+        setattr(o, k, val)
+    return o
+
+
+def sources_of(workload, amp=1.0):
+    """One unit source per RHS at the workload's source nodes."""
+    return [(ix, iy, iz, r, amp) for r, (ix, iy, iz) in enumerate(workload.sources)]
 
 
 def make_grid(shape, h, f, npml, v_ref, r_coef=1e-3):
@@ -167,6 +212,37 @@ class Context:
         self._check(lib().hx_row_coefficients(self._h, C.byref(grid), C.c_void_p(v.data_ptr()),
                                               float(shift_beta), C.c_void_p(coef.data_ptr()),
                                               _stream_ptr(stream)), "hx_row_coefficients")
+
+    def solve(self, grid, v, sources, nrhs, out, stream=None, check=True, **opts):
+        """hx_solve.  sources: [(ix, iy, iz, rhs, amp)] (amp complex), out:
+        complex128 (nrhs, nz, ny, nx) torch CUDA tensor.  Keyword options are
+        fields of hx_solve_opts.  Returns the report as a dict; raises HxError
+        on failure unless check=False (then report['status'] carries it)."""
+        o = default_opts(**opts)
+        src = (hx_source * len(sources))()
+        for k, (ix, iy, iz, rhs, amp) in enumerate(sources):
+            a = complex(amp)
+            src[k] = hx_source(int(ix), int(iy), int(iz), int(rhs), a.real, a.imag)
+        rep = hx_solve_report()
+        st = lib().hx_solve(self._h, C.byref(grid), C.c_void_p(v.data_ptr()), src, len(sources),
+                            int(nrhs), C.c_void_p(out.data_ptr()), C.byref(o), C.byref(rep),
+                            _stream_ptr(stream))
+        if check:
+            self._check(st, "hx_solve")
+        return rep.as_dict()
+
+    def profile(self, enable=True):
+        self._check(lib().hx_profile(self._h, 1 if enable else 0), "hx_profile")
+
+    def profile_read(self):
+        """{kind: (launches, total_ms, algo_bytes)} plus 'launches' (all kernels)."""
+        out = {}
+        n, ms, by = C.c_int64(0), C.c_double(0), C.c_double(0)
+        for name, k in list(PROF_KINDS.items()) + [("all", -1)]:
+            self._check(lib().hx_profile_read(self._h, k, C.byref(n), C.byref(ms), C.byref(by)),
+                        "hx_profile_read")
+            out[name] = (n.value, ms.value, by.value)
+        return out
 
     def assemble_csr(self, grid, v, shift_beta=0.0, stream=None):
         """-> (rowptr int64, col int32, val complex128) numpy arrays."""

@@ -1,4 +1,5 @@
 // C-ABI entry points: context, weight table, operator apply / coefficients.
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -153,9 +154,61 @@ OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double b
 template OpDesc<float> make_desc<float>(const hx_ctx*, const Level&, const float*, double);
 template OpDesc<double> make_desc<double>(const hx_ctx*, const Level&, const float*, double);
 
+namespace {
+std::atomic<long long> g_launches{0};
+}
+long long launch_count() { return g_launches.load(); }
+void count_launch(int n) { g_launches += n; }
+
+cudaEvent_t prof_begin(hx_ctx* ctx, cudaStream_t s) {
+  if (!ctx->prof_on) return nullptr;
+  cudaEvent_t e;
+  if (!ctx->prof_pool.empty()) {
+    e = ctx->prof_pool.back();
+    ctx->prof_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return nullptr;
+  }
+  cudaEventRecord(e, s);
+  return e;
+}
+
+void prof_end(hx_ctx* ctx, int kind, cudaEvent_t a, double bytes, cudaStream_t s) {
+  if (!ctx->prof_on || !a) return;
+  cudaEvent_t e;
+  if (!ctx->prof_pool.empty()) {
+    e = ctx->prof_pool.back();
+    ctx->prof_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    ctx->prof_pool.push_back(a);
+    return;
+  }
+  cudaEventRecord(e, s);
+  ctx->prof_pending.push_back({kind, a, e, bytes});
+}
+
+void prof_collect(hx_ctx* ctx) {
+  for (auto& p : ctx->prof_pending) {
+    float ms = 0;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      ctx->prof[p.kind].launches += 1;
+      ctx->prof[p.kind].ms += ms;
+      ctx->prof[p.kind].bytes += p.bytes;
+    }
+    ctx->prof_pool.push_back(p.a);
+    ctx->prof_pool.push_back(p.b);
+  }
+  ctx->prof_pending.clear();
+}
+
 }  // namespace hx
 
 hx_ctx::~hx_ctx() {
+  for (auto& p : prof_pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : prof_pool) cudaEventDestroy(e);
   solvers.clear();
   levels.clear();
   if (tab64) cudaFree(tab64);
@@ -260,6 +313,30 @@ int hx_apply_operator(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doub
   else
     e = launch_stencil(make_desc<double>(ctx, *lv, v_dev, shift_beta), kApply, x_dev, nullptr, y_dev, nrhs, N, 0.0, s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "apply launch");
+  return HX_OK;
+}
+
+int hx_profile(hx_ctx* ctx, int enable) {
+  if (!ctx) return HX_ERR_ARG;
+  prof_collect(ctx);
+  for (auto& p : ctx->prof) p = hx_ctx::ProfStat();
+  ctx->prof_on = enable != 0;
+  ctx->prof_launch_base = launch_count();
+  return HX_OK;
+}
+
+int hx_profile_read(hx_ctx* ctx, int kind, int64_t* launches, double* total_ms, double* algo_bytes) {
+  if (!ctx || kind < -1 || kind >= HX_PROF_KINDS) return fail(ctx, HX_ERR_ARG, "bad profile kind");
+  prof_collect(ctx);
+  if (kind == -1) {
+    if (launches) *launches = launch_count() - ctx->prof_launch_base;
+    if (total_ms) *total_ms = 0;
+    if (algo_bytes) *algo_bytes = 0;
+    return HX_OK;
+  }
+  if (launches) *launches = ctx->prof[kind].launches;
+  if (total_ms) *total_ms = ctx->prof[kind].ms;
+  if (algo_bytes) *algo_bytes = ctx->prof[kind].bytes;
   return HX_OK;
 }
 

@@ -52,6 +52,20 @@ struct hx_ctx {
   std::list<std::string> lru;
   std::map<std::string, std::unique_ptr<hx::Solver>> solvers;
   std::list<std::string> solver_lru;
+  // profiler (hx_profile): per-class launch count, time, algorithmic bytes
+  bool prof_on = false;
+  long long prof_launch_base = 0;
+  struct ProfStat {
+    long long launches = 0;
+    double ms = 0, bytes = 0;
+  } prof[4];
+  struct ProfPending {
+    int kind;
+    cudaEvent_t a, b;
+    double bytes;
+  };
+  std::vector<ProfPending> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
 
   ~hx_ctx();
 };
@@ -66,5 +80,13 @@ int check_grid(hx_ctx* ctx, const hx_grid* g);
 int get_level(hx_ctx* ctx, const hx_grid* g, const int n_level[3], double h_level, Level** out);
 template <typename T>
 OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double beta);
+
+// Profiler helpers: open/close an event pair around a launch of class `kind`
+// (no-ops when profiling is off); collect() folds finished pairs into the
+// counters (call after the stream is synchronised).
+cudaEvent_t prof_begin(hx_ctx* ctx, cudaStream_t s);
+void prof_end(hx_ctx* ctx, int kind, cudaEvent_t a, double bytes, cudaStream_t s);
+void prof_collect(hx_ctx* ctx);
+
 
 }  // namespace hx

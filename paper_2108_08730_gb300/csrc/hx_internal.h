@@ -38,15 +38,20 @@ struct OpDesc {
   int plain_lo[3], plain_hi[3];  // nodes whose up = dn = 1/h^2 exactly
 };
 
-enum StencilMode { kApply = 0, kResidual = 1, kJacobi = 2 };
+enum StencilMode { kApply = 0, kResidual = 1, kJacobi = 2, kJacobi0 = 3 };
 
-// Launch y = A x (kApply), y = b - A x (kResidual) or
-// y = x + omega_j D^{-1} (b - A x) (kJacobi) for nrhs fields of stride
-// `rstride` elements.  Returns a cudaError_t.
+// Launch y = A x (kApply), y = b - A x (kResidual; b == nullptr means b = 0),
+// y = x + omega_j D^{-1} (b - A x) (kJacobi) or y = omega_j D^{-1} b
+// (kJacobi0, the first sweep from x = 0; x is not read) for nrhs fields of
+// stride `rstride` elements.  Returns a cudaError_t.
 template <typename T>
 cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const void* b, void* y,
                            int nrhs, long long rstride, double omega_j, cudaStream_t s);
 
 cudaError_t launch_row_coefficients(const OpDesc<double>& op, double* coef, cudaStream_t s);
+
+// Kernels launched by the library in this process (every launcher counts).
+long long launch_count();
+void count_launch(int n);
 
 }  // namespace hx

@@ -213,8 +213,8 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
         if (r < rcount) {
           const long long o = (long long)(r0 + r) * rstride + off;
           C res = out[r];
-          if (MODE == kResidual || MODE == kJacobi) res = csub(b[o], res);
-          if (MODE == kJacobi) res = cfma(cscale(omega_j, dinv), res, cs[1][r]);
+          if (MODE == kResidual) res = b ? csub(b[o], res) : cmk(-res.x, -res.y);
+          if (MODE == kJacobi) res = cfma(cscale(omega_j, dinv), csub(b[o], res), cs[1][r]);
           y[o] = res;
         }
       }
@@ -225,6 +225,33 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
       cs[0][r] = cs[1][r]; es[0][r] = es[1][r]; ks[0][r] = ks[1][r];
       cs[1][r] = cs[2][r]; es[1][r] = es[2][r]; ks[1][r] = ks[2][r];
     }
+  }
+}
+
+// First damped-Jacobi sweep from a zero guess: y = omega_j D^{-1} b, with D
+// the row's diagonal coefficient (no neighbour reads).
+template <typename T, bool SHIFT>
+__global__ void jacobi0_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ b,
+                               typename CT<T>::type* __restrict__ y, int nrhs, long long rstride,
+                               T omega_j) {
+  using C = typename CT<T>::type;
+  const long long N = (long long)op.nx * op.ny * op.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % op.nx);
+    const int iy = (int)((i / op.nx) % op.ny);
+    const int iz = (int)(i / ((long long)op.nx * op.ny));
+    const PointW<T> pw = point_weights(op, __ldg(op.v + i));
+    const int id[3] = {ix, iy, iz};
+    C sdiag = czero<C>();
+    for (int d = 0; d < 3; ++d) {
+      const T* q = op.axis[d] + 4 * (size_t)id[d];
+      sdiag = cadd(sdiag, cmk(ldg(q) + ldg(q + 2), ldg(q + 1) + ldg(q + 3)));
+    }
+    const C mc = cmk(pw.m, SHIFT ? op.beta * pw.m : (T)0);
+    const C diag = cfma(mc, cmk(pw.w[4], (T)0), cscale(-pw.w[8], sdiag));
+    const C f = cscale(omega_j, crcp(diag));
+    for (int r = 0; r < nrhs; ++r) y[(long long)r * rstride + i] = cmul(f, b[(long long)r * rstride + i]);
   }
 }
 
@@ -290,6 +317,22 @@ cudaError_t launch_t(const OpDesc<T>& op, const void* x, const void* b, void* y,
   dim3 grid(bx, by, (unsigned)gz), block(TX, TY);
   stencil_kernel<T, MODE, SHIFT, RB, TX, TY><<<grid, block, 0, s>>>(
       op, (const C*)x, (const C*)b, (C*)y, nrhs, rstride, zchunk, (T)omega_j);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_j0(const OpDesc<T>& op, const void* b, void* y, int nrhs, long long rstride,
+                      double omega_j, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const long long N = (long long)op.nx * op.ny * op.nz;
+  long long blocks = (N + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (op.beta != 0)
+    jacobi0_kernel<T, true><<<(unsigned)blocks, 256, 0, s>>>(op, (const C*)b, (C*)y, nrhs, rstride, (T)omega_j);
+  else
+    jacobi0_kernel<T, false><<<(unsigned)blocks, 256, 0, s>>>(op, (const C*)b, (C*)y, nrhs, rstride, (T)omega_j);
+  count_launch(1);
   return cudaGetLastError();
 }
 
@@ -314,6 +357,7 @@ cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const v
     case kApply: return launch_m<T, kApply>(op, x, b, y, nrhs, rstride, omega_j, s);
     case kResidual: return launch_m<T, kResidual>(op, x, b, y, nrhs, rstride, omega_j, s);
     case kJacobi: return launch_m<T, kJacobi>(op, x, b, y, nrhs, rstride, omega_j, s);
+    case kJacobi0: return launch_j0<T>(op, b, y, nrhs, rstride, omega_j, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -328,6 +372,7 @@ cudaError_t launch_row_coefficients(const OpDesc<double>& op, double* coef, cuda
   long long blocks = (N + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
   row_coef_kernel<<<(unsigned)blocks, 256, 0, s>>>(op, (double2*)coef);
+  count_launch(1);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,475 @@
+// Batched vector kernels of the solver (see hx_vec.cuh).
+#include "hx_complex.cuh"
+#include "hx_internal.h"
+#include "hx_vec.cuh"
+
+namespace hx {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline dim3 grid_for(long long N, int R, int per_thread = 4) {
+  long long b = (N + (long long)kThreads * per_thread - 1) / ((long long)kThreads * per_thread);
+  if (b < 1) b = 1;
+  if (b > 4096) b = 4096;
+  return dim3((unsigned)b, (unsigned)R);
+}
+
+__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
+template <class C> __device__ __forceinline__ C from_d2(double2 a);
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
+
+// block-wide sum of a double2 (all threads get the result in lane 0 of warp 0)
+__device__ double2 block_sum(double2 v) {
+  __shared__ double2 sh[kThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double2 t = make_double2(0.0, 0.0);
+  if (w == 0) {
+    if (l < kThreads / 32) t = sh[l];
+    for (int o = 16; o > 0; o >>= 1) {
+      t.x += __shfl_down_sync(0xffffffffu, t.x, o);
+      t.y += __shfl_down_sync(0xffffffffu, t.y, o);
+    }
+  }
+  return t;
+}
+
+template <typename T, bool NORM>
+__global__ void __launch_bounds__(kThreads)
+dot_partial(const typename CT<T>::type* __restrict__ a, const typename CT<T>::type* __restrict__ b,
+            long long N, double2* __restrict__ part) {
+  using C = typename CT<T>::type;
+  const int r = blockIdx.y;
+  const C* ar = a + (long long)r * N;
+  const C* br = b + (long long)r * N;
+  T sx = 0, sy = 0;
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < N;
+       i += (long long)gridDim.x * kThreads) {
+    const C u = ar[i];
+    if (NORM) {
+      sx = fma(u.x, u.x, fma(u.y, u.y, sx));
+    } else {
+      const C w = br[i];
+      sx = fma(u.x, w.x, fma(u.y, w.y, sx));     // Re(conj(u) w)
+      sy = fma(u.x, w.y, fma(-u.y, w.x, sy));    // Im(conj(u) w)
+    }
+  }
+  const double2 t = block_sum(make_double2((double)sx, (double)sy));
+  if (threadIdx.x == 0) part[(long long)r * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(kThreads)
+dot_finish(const double2* __restrict__ part, int nblk, double2* out, double* out_re) {
+  const int r = blockIdx.x;
+  double2 s = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < nblk; i += kThreads) {
+    const double2 p = part[(long long)r * nblk + i];
+    s.x += p.x;
+    s.y += p.y;
+  }
+  const double2 t = block_sum(s);
+  if (threadIdx.x == 0) {
+    if (out) out[r] = t;
+    if (out_re) out_re[r] = t.x;
+  }
+}
+
+template <typename T>
+__global__ void bicg_p_k(typename CT<T>::type* __restrict__ p, const typename CT<T>::type* __restrict__ r,
+                         const typename CT<T>::type* __restrict__ v, const double2* beta,
+                         const double2* omega, long long N) {
+  using C = typename CT<T>::type;
+  const int k = blockIdx.y;
+  const C be = from_d2<C>(beta[k]), om = from_d2<C>(omega[k]);
+  const long long o = (long long)k * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const C pv = p[o + i], vv = v[o + i];
+    const C t = csub(pv, cmul(om, vv));
+    p[o + i] = cfma(be, t, r[o + i]);
+  }
+}
+
+template <typename T>
+__global__ void bicg_s_k(typename CT<T>::type* __restrict__ sv, const typename CT<T>::type* __restrict__ r,
+                         const typename CT<T>::type* __restrict__ v, const double2* alpha, long long N) {
+  using C = typename CT<T>::type;
+  const int k = blockIdx.y;
+  const C al = from_d2<C>(alpha[k]);
+  const C mal = cmk(-al.x, -al.y);
+  const long long o = (long long)k * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x)
+    sv[o + i] = cfma(mal, v[o + i], r[o + i]);
+}
+
+template <typename T>
+__global__ void bicg_xr_k(typename CT<T>::type* __restrict__ x, typename CT<T>::type* __restrict__ r,
+                          const typename CT<T>::type* __restrict__ sv,
+                          const typename CT<T>::type* __restrict__ ph,
+                          const typename CT<T>::type* __restrict__ sh,
+                          const typename CT<T>::type* __restrict__ t, const double2* alpha,
+                          const double2* omega, long long N) {
+  using C = typename CT<T>::type;
+  const int k = blockIdx.y;
+  const C al = from_d2<C>(alpha[k]), om = from_d2<C>(omega[k]);
+  const C mom = cmk(-om.x, -om.y);
+  const long long o = (long long)k * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    x[o + i] = cfma(om, sh[o + i], cfma(al, ph[o + i], x[o + i]));
+    r[o + i] = cfma(mom, t[o + i], sv[o + i]);
+  }
+}
+
+// full weighting: coarse node I <- fine nodes 2I + s, s in {-1,0,1}^3, weight
+// prod_d (1/2)^{|s_d|} / 8; fine nodes outside the grid are zero.
+template <typename T>
+__global__ void restrict_k(const typename CT<T>::type* __restrict__ f, int fx, int fy, int fz,
+                           typename CT<T>::type* __restrict__ c, int cx, int cy, int cz) {
+  using C = typename CT<T>::type;
+  const long long Nc = (long long)cx * cy * cz, Nf = (long long)fx * fy * fz;
+  const int r = blockIdx.y;
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < Nc;
+       I += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)(I % cx), Y = (int)((I / cx) % cy), Z = (int)(I / ((long long)cx * cy));
+    C acc = czero<C>();
+    for (int sz = -1; sz <= 1; ++sz) {
+      const int z = 2 * Z + sz;
+      if (z < 0 || z >= fz) continue;
+      for (int sy = -1; sy <= 1; ++sy) {
+        const int y = 2 * Y + sy;
+        if (y < 0 || y >= fy) continue;
+        for (int sx = -1; sx <= 1; ++sx) {
+          const int x = 2 * X + sx;
+          if (x < 0 || x >= fx) continue;
+          const T w = (T)1 / (T)(8 << (abs(sx) + abs(sy) + abs(sz)));
+          acc = cfmar(w, f[(long long)r * Nf + ((long long)z * fy + y) * fx + x], acc);
+        }
+      }
+    }
+    c[(long long)r * Nc + I] = acc;
+  }
+}
+
+// trilinear prolongation added to the fine field
+template <typename T>
+__global__ void prolong_k(typename CT<T>::type* __restrict__ f, int fx, int fy, int fz,
+                          const typename CT<T>::type* __restrict__ c, int cx, int cy, int cz) {
+  using C = typename CT<T>::type;
+  const long long Nc = (long long)cx * cy * cz, Nf = (long long)fx * fy * fz;
+  const int r = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Nf;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % fx), y = (int)((i / fx) % fy), z = (int)(i / ((long long)fx * fy));
+    int ix[2], iy[2], iz[2];
+    T wx[2], wy[2], wz[2];
+    auto split = [](int p, int nc, int* id, T* w) {
+      if ((p & 1) == 0) { id[0] = p / 2; w[0] = 1; id[1] = 0; w[1] = 0; }
+      else {
+        id[0] = p / 2; w[0] = (T)0.5;
+        id[1] = p / 2 + 1; w[1] = p / 2 + 1 < nc ? (T)0.5 : (T)0;
+        if (id[1] >= nc) id[1] = nc - 1;
+      }
+    };
+    split(x, cx, ix, wx);
+    split(y, cy, iy, wy);
+    split(z, cz, iz, wz);
+    C acc = czero<C>();
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int d = 0; d < 2; ++d) {
+          const T w = wz[a] * wy[b] * wx[d];
+          if (w != (T)0)
+            acc = cfmar(w, c[(long long)r * Nc + ((long long)iz[a] * cy + iy[b]) * cx + ix[d]], acc);
+        }
+    f[(long long)r * Nf + i] = cadd(f[(long long)r * Nf + i], acc);
+  }
+}
+
+__global__ void inject_v_k(const float* __restrict__ vf, int fx, int fy, float* __restrict__ vc,
+                           int cx, int cy, int cz) {
+  const long long Nc = (long long)cx * cy * cz;
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < Nc;
+       I += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)(I % cx), Y = (int)((I / cx) % cy), Z = (int)(I / ((long long)cx * cy));
+    vc[I] = vf[((long long)(2 * Z) * fy + 2 * Y) * fx + 2 * X];
+  }
+}
+
+__global__ void cast_scale_k(const double2* __restrict__ r64, float2* __restrict__ r32,
+                             const double* scale, long long N) {
+  const int k = blockIdx.y;
+  const double s = scale[k];
+  const long long o = (long long)k * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 a = r64[o + i];
+    r32[o + i] = make_float2((float)(a.x * s), (float)(a.y * s));
+  }
+}
+
+template <class D>
+__global__ void axpy_mixed_k(double2* __restrict__ x, const D* __restrict__ d,
+                             const double* scale, long long N) {
+  const int k = blockIdx.y;
+  const double s = scale[k];
+  const long long o = (long long)k * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const D a = d[o + i];
+    double2 v = x[o + i];
+    v.x = fma(s, (double)a.x, v.x);
+    v.y = fma(s, (double)a.y, v.y);
+    x[o + i] = v;
+  }
+}
+
+template <typename T>
+__global__ void add_sources_k(typename CT<T>::type* r, long long N, const SourceEntry* e, int n) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    T* p = (T*)(r + (long long)e[k].rhs * N + e[k].idx);
+    atomicAdd(p, (T)e[k].re);
+    atomicAdd(p + 1, (T)e[k].im);
+  }
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ bool tiny(double2 a) { return !(a.x * a.x + a.y * a.y > 1e-300); }
+
+__global__ void scal_beta_k(double2* beta, double2* rho, const double2* rho_new, const double2* alpha,
+                            const double2* omega, const int* active, int* brk, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  if (!active[r]) { beta[r] = make_double2(0, 0); return; }
+  if (tiny(rho[r]) || tiny(omega[r])) { beta[r] = make_double2(0, 0); brk[r] = 1; return; }
+  beta[r] = cdiv(cmul(rho_new[r], alpha[r]), cmul(rho[r], omega[r]));
+  rho[r] = rho_new[r];
+}
+
+__global__ void scal_alpha_k(double2* alpha, const double2* rho, const double2* rv, int* active,
+                             int* brk, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  if (!active[r]) { alpha[r] = make_double2(0, 0); return; }
+  if (tiny(rv[r])) { alpha[r] = make_double2(0, 0); active[r] = 0; brk[r] = 1; return; }
+  alpha[r] = cdiv(rho[r], rv[r]);
+}
+
+__global__ void scal_omega_k(double2* omega, const double2* ts, const double* tt, int* active,
+                             int* brk, int R) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  if (!active[r]) { omega[r] = make_double2(0, 0); return; }
+  if (!(tt[r] > 1e-300)) { omega[r] = make_double2(0, 0); active[r] = 0; brk[r] = 1; return; }
+  omega[r] = make_double2(ts[r].x / tt[r], ts[r].y / tt[r]);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+dense_matvec_k(const typename CT<T>::type* __restrict__ M, const typename CT<T>::type* __restrict__ b,
+               typename CT<T>::type* __restrict__ out, long long n) {
+  using C = typename CT<T>::type;
+  const long long i = blockIdx.x;
+  const int r = blockIdx.y;
+  const C* row = M + i * n;
+  const C* br = b + (long long)r * n;
+  double sx = 0, sy = 0;
+  for (long long j = threadIdx.x; j < n; j += kThreads) {
+    const C a = row[j], x = br[j];
+    sx += (double)a.x * x.x - (double)a.y * x.y;
+    sy += (double)a.x * x.y + (double)a.y * x.x;
+  }
+  const double2 t = block_sum(make_double2(sx, sy));
+  if (threadIdx.x == 0) out[(long long)r * n + i] = from_d2<C>(t);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_dense_matvec(const void* M, const void* b, void* out, long long n, int R,
+                                cudaStream_t s) {
+  using C = typename CT<T>::type;
+  dense_matvec_k<T><<<dim3((unsigned)n, R), kThreads, 0, s>>>((const C*)M, (const C*)b, (C*)out, n);
+  count_launch(1);
+  return cudaGetLastError();
+}
+template cudaError_t launch_dense_matvec<float>(const void*, const void*, void*, long long, int, cudaStream_t);
+template cudaError_t launch_dense_matvec<double>(const void*, const void*, void*, long long, int, cudaStream_t);
+
+int reduce_blocks(long long N) {
+  long long b = (N + 1023) / 1024;
+  if (b < 1) b = 1;
+  if (b > 2048) b = 2048;
+  return (int)b;
+}
+
+template <typename T>
+cudaError_t launch_dot(const void* a, const void* b, long long N, int R, double2* part, double2* out,
+                       cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const int nb = reduce_blocks(N);
+  dot_partial<T, false><<<dim3(nb, R), kThreads, 0, s>>>((const C*)a, (const C*)b, N, part);
+  dot_finish<<<R, kThreads, 0, s>>>(part, nb, out, nullptr);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_norm2(const void* a, long long N, int R, double2* part, double* out, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const int nb = reduce_blocks(N);
+  dot_partial<T, true><<<dim3(nb, R), kThreads, 0, s>>>((const C*)a, (const C*)a, N, part);
+  dot_finish<<<R, kThreads, 0, s>>>(part, nb, nullptr, out);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bicg_p(void* p, const void* r, const void* v, const double2* beta,
+                          const double2* omega, long long N, int R, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  bicg_p_k<T><<<grid_for(N, R), kThreads, 0, s>>>((C*)p, (const C*)r, (const C*)v, beta, omega, N);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bicg_s(void* sv, const void* r, const void* v, const double2* alpha, long long N,
+                          int R, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  bicg_s_k<T><<<grid_for(N, R), kThreads, 0, s>>>((C*)sv, (const C*)r, (const C*)v, alpha, N);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_bicg_xr(void* x, void* r, const void* sv, const void* phat, const void* shat,
+                           const void* t, const double2* alpha, const double2* omega, long long N,
+                           int R, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  bicg_xr_k<T><<<grid_for(N, R), kThreads, 0, s>>>((C*)x, (C*)r, (const C*)sv, (const C*)phat,
+                                                   (const C*)shat, (const C*)t, alpha, omega, N);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_restrict(const void* fine, const int nf[3], void* coarse, const int nc[3], int R,
+                            cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const long long Nc = (long long)nc[0] * nc[1] * nc[2];
+  restrict_k<T><<<grid_for(Nc, R, 1), kThreads, 0, s>>>((const C*)fine, nf[0], nf[1], nf[2], (C*)coarse,
+                                                        nc[0], nc[1], nc[2]);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong_add(void* fine, const int nf[3], const void* coarse, const int nc[3], int R,
+                               cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const long long Nf = (long long)nf[0] * nf[1] * nf[2];
+  prolong_k<T><<<grid_for(Nf, R, 1), kThreads, 0, s>>>((C*)fine, nf[0], nf[1], nf[2], (const C*)coarse,
+                                                       nc[0], nc[1], nc[2]);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_inject_velocity(const float* vf, const int nf[3], float* vc, const int nc[3],
+                                   cudaStream_t s) {
+  const long long Nc = (long long)nc[0] * nc[1] * nc[2];
+  inject_v_k<<<grid_for(Nc, 1, 1), kThreads, 0, s>>>(vf, nf[0], nf[1], vc, nc[0], nc[1], nc[2]);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_scale(const double2* r64, float2* r32, const double* scale, long long N, int R,
+                              cudaStream_t s) {
+  cast_scale_k<<<grid_for(N, R), kThreads, 0, s>>>(r64, r32, scale, N);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_mixed(double2* x64, const float2* d32, const double* scale, long long N, int R,
+                              cudaStream_t s) {
+  axpy_mixed_k<float2><<<grid_for(N, R), kThreads, 0, s>>>(x64, d32, scale, N);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_c128(double2* x64, const double2* d64, const double* scale, long long N, int R,
+                             cudaStream_t s) {
+  axpy_mixed_k<double2><<<grid_for(N, R), kThreads, 0, s>>>(x64, d64, scale, N);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_copy(void* y, const void* x, long long n, cudaStream_t s) {
+  return cudaMemcpyAsync(y, x, n * 2 * sizeof(T), cudaMemcpyDeviceToDevice, s);
+}
+
+template <typename T>
+cudaError_t launch_add_sources(void* r, long long N, const SourceEntry* e, int n, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  if (n <= 0) return cudaSuccess;
+  add_sources_k<T><<<(n + 127) / 128, 128, 0, s>>>((C*)r, N, e, n);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scal_beta(double2* beta, double2* rho, const double2* rho_new, const double2* alpha,
+                             const double2* omega, const int* active, int* brk, int R, cudaStream_t s) {
+  scal_beta_k<<<(R + 127) / 128, 128, 0, s>>>(beta, rho, rho_new, alpha, omega, active, brk, R);
+  count_launch(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_scal_alpha(double2* alpha, const double2* rho, const double2* rv, int* active,
+                              int* brk, int R, cudaStream_t s) {
+  scal_alpha_k<<<(R + 127) / 128, 128, 0, s>>>(alpha, rho, rv, active, brk, R);
+  count_launch(1);
+  return cudaGetLastError();
+}
+cudaError_t launch_scal_omega(double2* omega, const double2* ts, const double* tt, int* active,
+                              int* brk, int R, cudaStream_t s) {
+  scal_omega_k<<<(R + 127) / 128, 128, 0, s>>>(omega, ts, tt, active, brk, R);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+#define HX_INST(T)                                                                                  \
+  template cudaError_t launch_dot<T>(const void*, const void*, long long, int, double2*, double2*, \
+                                     cudaStream_t);                                                \
+  template cudaError_t launch_norm2<T>(const void*, long long, int, double2*, double*,             \
+                                       cudaStream_t);                                              \
+  template cudaError_t launch_bicg_p<T>(void*, const void*, const void*, const double2*,           \
+                                        const double2*, long long, int, cudaStream_t);             \
+  template cudaError_t launch_bicg_s<T>(void*, const void*, const void*, const double2*,           \
+                                        long long, int, cudaStream_t);                             \
+  template cudaError_t launch_bicg_xr<T>(void*, void*, const void*, const void*, const void*,      \
+                                         const void*, const double2*, const double2*, long long,   \
+                                         int, cudaStream_t);                                       \
+  template cudaError_t launch_restrict<T>(const void*, const int*, void*, const int*, int,         \
+                                          cudaStream_t);                                           \
+  template cudaError_t launch_prolong_add<T>(void*, const int*, const void*, const int*, int,      \
+                                             cudaStream_t);                                        \
+  template cudaError_t launch_copy<T>(void*, const void*, long long, cudaStream_t);                \
+  template cudaError_t launch_add_sources<T>(void*, long long, const SourceEntry*, int,            \
+                                             cudaStream_t);
+HX_INST(float)
+HX_INST(double)
+
+}  // namespace hx
