@@ -151,6 +151,30 @@ int hx_assemble_csr(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
                     double shift_beta, int64_t* rowptr, int32_t* col,
                     double* val, int64_t nnz_cap, int64_t* nnz_out, void* stream);
 
+/* Largest grid (nx*ny*nz) hx_assemble_csr_noalloc accepts: a 27^3 grid. */
+#define HX_NOALLOC_MAX_POINTS 19683
+
+/* hx_assemble_csr for callers that may not allocate device memory.  The
+ * paper has no counterpart: this is a deployment convenience.  Some callers
+ * cannot call cudaMalloc/cudaFree where they need the matrix -- their device
+ * memory belongs to another allocator, they must avoid the device-wide
+ * synchronisation of cudaFree, or their memory budget is fixed after
+ * start-up.  hx_assemble_csr allocates a temporary device buffer for the
+ * coefficients; this entry point allocates nothing and uses a fixed scratch
+ * array compiled into the library (about 8.7 MB held on every GPU that loads
+ * the library, until the process exits).
+ *   Same arguments, output and result as hx_assemble_csr, for grids of at
+ *   most HX_NOALLOC_MAX_POINTS points (HX_ERR_ARG with a message otherwise).
+ *   The first call on each device looks up the scratch array's device address
+ *   (cudaGetSymbolAddress) while the context's device is current; make that
+ *   first call before any stream capture.
+ *   All calls share the one scratch array: calls whose device work may overlap
+ *   (other host threads or streams) race and must be serialised by the caller.
+ *   Synchronises `stream`. */
+int hx_assemble_csr_noalloc(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
+                            double shift_beta, int64_t* rowptr, int32_t* col,
+                            double* val, int64_t nnz_cap, int64_t* nnz_out, void* stream);
+
 /* ---------------------------------------------------------------- solve */
 
 enum { HX_SOLVE_MIXED = 0, HX_SOLVE_FP64 = 1 };

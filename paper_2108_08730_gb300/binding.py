@@ -22,7 +22,10 @@ STATUS = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_OOM", -3: "HX_ERR_NOT_CONVER
 # every symbol include/hx27.h declares (checked by tests/test_abi.py)
 EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_error",
            "hx_set_table", "hx_apply_operator", "hx_row_coefficients", "hx_assemble_csr",
-           "hx_solve_default_opts", "hx_solve", "hx_profile", "hx_profile_read")
+           "hx_solve_default_opts", "hx_solve", "hx_profile", "hx_profile_read",
+           "hx_assemble_csr_noalloc")
+
+NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
 
 PROF_KINDS = {"apply32": 0, "smooth32": 1, "apply64": 2, "smooth64": 3}
 
@@ -91,6 +94,7 @@ def lib():
     L.hx_solve_default_opts.restype = None
     L.hx_solve.argtypes = [vp, C.POINTER(hx_grid), vp, C.POINTER(hx_source), i, i, vp,
                            C.POINTER(hx_solve_opts), C.POINTER(hx_solve_report), vp]
+    L.hx_assemble_csr_noalloc.argtypes = L.hx_assemble_csr.argtypes
     L.hx_profile.argtypes = [vp, i]
     L.hx_profile_read.argtypes = [vp, i, C.POINTER(C.c_int64), dp, dp]
     for name in EXPORTS:
@@ -256,5 +260,22 @@ class Context:
             self._h, C.byref(grid), C.c_void_p(v.data_ptr()), float(shift_beta),
             rowptr.ctypes.data_as(C.POINTER(C.c_int64)), col.ctypes.data_as(C.POINTER(C.c_int32)),
             _dptr(val), cap, C.byref(nnz), _stream_ptr(stream)), "hx_assemble_csr")
+        n = nnz.value
+        return rowptr, col[:n].copy(), val[:2 * n].view(np.complex128).copy()
+
+    def assemble_csr_noalloc(self, grid, v, shift_beta=0.0, stream=None):
+        """hx_assemble_csr_noalloc: same result as assemble_csr without any
+        device allocation by the library (grids of at most NOALLOC_MAX_POINTS
+        points).  The numpy output arrays are host memory owned by Python."""
+        N = grid.nx * grid.ny * grid.nz
+        cap = 27 * N
+        rowptr = np.zeros(N + 1, dtype=np.int64)
+        col = np.zeros(cap, dtype=np.int32)
+        val = np.zeros(2 * cap, dtype=np.float64)
+        nnz = C.c_int64(0)
+        self._check(lib().hx_assemble_csr_noalloc(
+            self._h, C.byref(grid), C.c_void_p(v.data_ptr()), float(shift_beta),
+            rowptr.ctypes.data_as(C.POINTER(C.c_int64)), col.ctypes.data_as(C.POINTER(C.c_int32)),
+            _dptr(val), cap, C.byref(nnz), _stream_ptr(stream)), "hx_assemble_csr_noalloc")
         n = nnz.value
         return rowptr, col[:n].copy(), val[:2 * n].view(np.complex128).copy()
