@@ -198,6 +198,14 @@ typedef struct {
   int source_spread;     /* 0: grid delta (default); 1: consistent-mass spread    */
   int initial_guess;     /* 1: wavefield_dev holds the starting iterate           */
   int check_every;       /* iterations between host convergence checks (1)       */
+  int coarse_galerkin;   /* 1: coarse operators R A P (Galerkin); 0 (default):
+                            the stencil rediscretised at 2^l h                    */
+  double pml_cap;        /* the preconditioner's PML damping is capped at
+                            gamma <= pml_cap * omega (default 1; 0 = no cap).
+                            Damped Jacobi diverges where the stretching rotates
+                            one axis's coefficients far from the others; the
+                            preconditioner only has to approximate A^-1, and the
+                            Krylov operator keeps the true PML.                   */
 } hx_solve_opts;
 
 typedef struct {
@@ -241,11 +249,13 @@ int hx_profile_read(hx_ctx* ctx, int kind, int64_t* launches, double* total_ms,
  * sources (Section 3.1), GA weights per row, with the given grid/PML.
  * Method (not in the paper, which uses a sparse direct solver): BiCGStab
  * right-preconditioned by a V-cycle of the complex-shifted operator
- * (omega^2 -> (1 + i beta) omega^2) on grids coarsened by 2 (vertex-centred,
- * velocity injected, same stencil and PML profile rediscretised at 2^l h,
- * 1/G clamped to the table), damped-Jacobi smoothing, full-weighting
- * restriction, trilinear prolongation.  Mixed mode runs that in complex64 and
- * corrects an FP64 iterate with FP64 residuals until opts.tol.
+ * (omega^2 -> (1 + i beta) omega^2) on vertex-centred grids coarsened by 2,
+ * with Galerkin coarse operators R A P (or, with coarse_galerkin = 0, the
+ * same stencil and PML profile rediscretised at 2^l h on injected
+ * velocities, 1/G clamped to the table), damped-Jacobi smoothing,
+ * full-weighting restriction, trilinear prolongation and an exact dense solve
+ * of the coarsest level (at most 512 nodes).  Mixed mode runs that in
+ * complex64 and corrects an FP64 iterate with FP64 residuals until opts.tol.
  *   v_dev: float32 [nz][ny][nx], every value finite, > 0 and with
  *          f h / v <= the table's largest 1/G (HX_ERR_ARG otherwise).
  *   src:   host array of nsrc sources; every rhs in [0, nrhs) must have one.

@@ -65,11 +65,11 @@ int check_grid(hx_ctx* ctx, const hx_grid* g) {
   return HX_OK;
 }
 
-int get_level(hx_ctx* ctx, const hx_grid* g, const int nl[3], double hl, Level** out) {
+int get_level(hx_ctx* ctx, const hx_grid* g, const int nl[3], double hl, Level** out, double gamma_cap) {
   char key[512];
-  std::snprintf(key, sizeof(key), "%d %d %d %.17g %.17g %d %d %d %d %d %d %.17g %.17g | %d %d %d %.17g",
+  std::snprintf(key, sizeof(key), "%d %d %d %.17g %.17g %d %d %d %d %d %d %.17g %.17g | %d %d %d %.17g c%.17g",
                 g->nx, g->ny, g->nz, g->h, g->f, g->npml[0], g->npml[1], g->npml[2], g->npml[3],
-                g->npml[4], g->npml[5], g->v_ref, g->r_coef, nl[0], nl[1], nl[2], hl);
+                g->npml[4], g->npml[5], g->v_ref, g->r_coef, nl[0], nl[1], nl[2], hl, gamma_cap);
   auto it = ctx->levels.find(key);
   if (it != ctx->levels.end()) {
     ctx->lru.remove(key);
@@ -88,8 +88,12 @@ int get_level(hx_ctx* ctx, const hx_grid* g, const int nl[3], double hl, Level**
   lv->f = g->f;
   for (int d = 0; d < 3; ++d) {
     lv->n[d] = nl[d];
-    const Profile1D prof =
+    Profile1D prof =
         Profile1D::from_grid(nf[d], g->h, g->npml[2 * d], g->npml[2 * d + 1], g->v_ref, g->r_coef);
+    if (gamma_cap > 0) {
+      prof.g0_lo = std::min(prof.g0_lo, gamma_cap * omega);
+      prof.g0_hi = std::min(prof.g0_hi, gamma_cap * omega);
+    }
     std::vector<double> a64(4 * (size_t)nl[d]);
     std::vector<float> a32(4 * (size_t)nl[d]);
     const double ih2 = 1.0 / (hl * hl);

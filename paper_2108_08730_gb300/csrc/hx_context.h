@@ -77,7 +77,10 @@ int cuda_fail(hx_ctx* ctx, cudaError_t e, const char* where);
 int check_grid(hx_ctx* ctx, const hx_grid* g);
 // Level for grid g evaluated at spacing h_level with n_level nodes per axis
 // (level 0: the grid itself).  Returned pointer is owned by ctx.
-int get_level(hx_ctx* ctx, const hx_grid* g, const int n_level[3], double h_level, Level** out);
+// gamma_cap > 0 caps the PML damping at gamma <= gamma_cap * omega (used by the
+// multigrid preconditioner); 0 = the grid's own profile.
+int get_level(hx_ctx* ctx, const hx_grid* g, const int n_level[3], double h_level, Level** out,
+              double gamma_cap = 0.0);
 template <typename T>
 OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double beta);
 

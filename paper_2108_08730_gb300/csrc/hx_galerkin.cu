@@ -1,0 +1,221 @@
+// Galerkin coarse operators of the multigrid preconditioner and the kernels
+// that apply stored 27-point operators on the coarse levels.
+//
+// Not in the paper.  A_c = R A P with R full weighting and P trilinear
+// interpolation on vertex-centred grids (R = P^T / 8): with a 27-point fine
+// operator the coarse operator is again 27-point.  The fine operator of level
+// 0 is formed on the fly (the adaptive row of Eqs. 4-8 with the shifted mass);
+// deeper levels take the stored coefficients of the level above.  Coefficients
+// are stored offset-major, coef[k][i] for offset k = (dk+1)*9 + (dj+1)*3 +
+// (di+1), so a warp reads each offset's coefficients coalesced.
+#include "hx_complex.cuh"
+#include "hx_galerkin.cuh"
+#include "hx_internal.h"
+
+namespace hx {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ void fine_row(const OpDesc<T>& op, int ix, int iy, int iz,
+                                         typename CT<T>::type c[27]) {
+  using C = typename CT<T>::type;
+  const long long i = ix + (long long)op.nx * (iy + (long long)op.ny * iz);
+  const T vt = (T)__ldg(op.v + i);
+  const T iv = (T)1 / vt;
+  T u = op.u_scale * iv;
+  const T umax = (T)(op.n_g - 1);
+  u = u < (T)0 ? (T)0 : (u > umax ? umax : u);
+  int i0 = (int)u;
+  if (i0 > op.n_g - 2) i0 = op.n_g - 2;
+  const T t = u - (T)i0;
+  const T* a = op.tab + (size_t)i0 * kTabW;
+  T w[11];
+#pragma unroll
+  for (int k = 0; k < 11; ++k) w[k] = fma(t, __ldg(a + kTabW + k) - __ldg(a + k), __ldg(a + k));
+  const T m = op.omega2 * iv * iv;
+  const C mc = cmk(m, op.beta * m);
+  const T tw[3] = {w[8], w[9], w[10]};
+  const int id[3] = {ix, iy, iz};
+  C D[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const T* q = op.axis[d] + 4 * (size_t)id[d];
+    const C up = cmk(__ldg(q), __ldg(q + 1)), dn = cmk(__ldg(q + 2), __ldg(q + 3));
+    D[d][2] = up;
+    D[d][0] = dn;
+    D[d][1] = cmk(-(up.x + dn.x), -(up.y + dn.y));
+  }
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dk = k / 9 - 1;
+    C v = cscale(tw[abs(dj) + abs(dk)], D[0][di + 1]);
+    v = cfmar(tw[abs(di) + abs(dk)], D[1][dj + 1], v);
+    v = cfmar(tw[abs(di) + abs(dj)], D[2][dk + 1], v);
+    c[k] = cfma(mc, cmk(w[4 + abs(di) + abs(dj) + abs(dk)], (T)0), v);
+  }
+}
+
+// trilinear weight of fine offset r (relative to 2I, in [-2, 2]) for coarse
+// offset D in {-1, 0, 1}
+__device__ __forceinline__ float pw1(int r, int D) {
+  const int d = r - 2 * D;
+  return d == 0 ? 1.f : (d == 1 || d == -1 ? 0.5f : 0.f);
+}
+
+template <typename T, bool ONFLY>
+__global__ void __launch_bounds__(128)
+galerkin_k(OpDesc<T> op, const typename CT<T>::type* __restrict__ cf, int fx, int fy, int fz,
+           typename CT<T>::type* __restrict__ cc, int cx, int cy, int cz) {
+  using C = typename CT<T>::type;
+  const long long Nc = (long long)cx * cy * cz, Nf = (long long)fx * fy * fz;
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < Nc;
+       I += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)(I % cx), Y = (int)((I / cx) % cy), Z = (int)(I / ((long long)cx * cy));
+    C acc[27];
+#pragma unroll
+    for (int k = 0; k < 27; ++k) acc[k] = czero<C>();
+    for (int s = 0; s < 27; ++s) {
+      const int sx = s % 3 - 1, sy = (s / 3) % 3 - 1, sz = s / 9 - 1;
+      const int ix = 2 * X + sx, iy = 2 * Y + sy, iz = 2 * Z + sz;
+      if (ix < 0 || ix >= fx || iy < 0 || iy >= fy || iz < 0 || iz >= fz) continue;
+      const T wr = (T)1 / (T)(8 << (abs(sx) + abs(sy) + abs(sz)));
+      C a[27];
+      if (ONFLY) {
+        fine_row<T>(op, ix, iy, iz, a);
+      } else {
+        const long long i = ix + (long long)fx * (iy + (long long)fy * iz);
+#pragma unroll
+        for (int k = 0; k < 27; ++k) a[k] = cf[(long long)k * Nf + i];
+      }
+#pragma unroll
+      for (int k = 0; k < 27; ++k) {
+        const int oi = k % 3 - 1, oj = (k / 3) % 3 - 1, ok = k / 9 - 1;
+        const int jx = ix + oi, jy = iy + oj, jz = iz + ok;
+        if (jx < 0 || jx >= fx || jy < 0 || jy >= fy || jz < 0 || jz >= fz) continue;
+        const C c = cscale(wr, a[k]);
+        const int rx = sx + oi, ry = sy + oj, rz = sz + ok;   // in [-2, 2]
+#pragma unroll
+        for (int q = 0; q < 27; ++q) {
+          const int Dx = q % 3 - 1, Dy = (q / 3) % 3 - 1, Dz = q / 9 - 1;
+          const float p = pw1(rx, Dx) * pw1(ry, Dy) * pw1(rz, Dz);
+          if (p != 0.f) {
+            const int Jx = X + Dx, Jy = Y + Dy, Jz = Z + Dz;
+            if (Jx >= 0 && Jx < cx && Jy >= 0 && Jy < cy && Jz >= 0 && Jz < cz)
+              acc[q] = cfmar((T)p, c, acc[q]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 27; ++k) cc[(long long)k * Nc + I] = acc[k];
+  }
+}
+
+// y = A x / b - A x / x + w D^-1 (b - A x) / w D^-1 b with stored coefficients
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+stored_stencil_k(const typename CT<T>::type* __restrict__ coef, int nx, int ny, int nz,
+                 const typename CT<T>::type* __restrict__ x, const typename CT<T>::type* __restrict__ b,
+                 typename CT<T>::type* __restrict__ y, int R, T omega_j) {
+  using C = typename CT<T>::type;
+  const long long N = (long long)nx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((long long)nx * ny));
+    const C dg = coef[13 * N + i];
+    const C dinv = cscale(omega_j, crcp(dg));
+    if (MODE == kJacobi0) {
+      for (int r = 0; r < R; ++r) y[(long long)r * N + i] = cmul(dinv, b[(long long)r * N + i]);
+      continue;
+    }
+    for (int r = 0; r < R; ++r) {
+      const C* xr = x + (long long)r * N;
+      C acc = czero<C>();
+#pragma unroll
+      for (int k = 0; k < 27; ++k) {
+        const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dk = k / 9 - 1;
+        const int jx = ix + di, jy = iy + dj, jz = iz + dk;
+        if (jx < 0 || jx >= nx || jy < 0 || jy >= ny || jz < 0 || jz >= nz) continue;
+        acc = cfma(coef[(long long)k * N + i], xr[i + di + (long long)nx * (dj + (long long)ny * dk)], acc);
+      }
+      const long long o = (long long)r * N + i;
+      C res = acc;
+      if (MODE == kResidual) res = csub(b[o], acc);
+      if (MODE == kJacobi) res = cfma(dinv, csub(b[o], acc), xr[i]);
+      y[o] = res;
+    }
+  }
+}
+
+unsigned blocks_for(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_galerkin_onfly(const OpDesc<T>& fine, void* coarse_coef, const int nc[3],
+                                  cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const long long Nc = (long long)nc[0] * nc[1] * nc[2];
+  galerkin_k<T, true><<<blocks_for(Nc, 128, 152 * 64), 128, 0, s>>>(
+      fine, nullptr, fine.nx, fine.ny, fine.nz, (C*)coarse_coef, nc[0], nc[1], nc[2]);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_galerkin_stored(const void* fine_coef, const int nf[3], void* coarse_coef,
+                                   const int nc[3], cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const long long Nc = (long long)nc[0] * nc[1] * nc[2];
+  OpDesc<T> dummy{};
+  galerkin_k<T, false><<<blocks_for(Nc, 128, 152 * 64), 128, 0, s>>>(
+      dummy, (const C*)fine_coef, nf[0], nf[1], nf[2], (C*)coarse_coef, nc[0], nc[1], nc[2]);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stored_stencil(const void* coef, const int n[3], int mode, const void* x,
+                                  const void* b, void* y, int R, double omega_j, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const long long N = (long long)n[0] * n[1] * n[2];
+  const unsigned g = blocks_for(N, 256, 152 * 16);
+  switch (mode) {
+    case kApply:
+      stored_stencil_k<T, kApply><<<g, 256, 0, s>>>((const C*)coef, n[0], n[1], n[2], (const C*)x,
+                                                    (const C*)b, (C*)y, R, (T)omega_j);
+      break;
+    case kResidual:
+      stored_stencil_k<T, kResidual><<<g, 256, 0, s>>>((const C*)coef, n[0], n[1], n[2], (const C*)x,
+                                                       (const C*)b, (C*)y, R, (T)omega_j);
+      break;
+    case kJacobi:
+      stored_stencil_k<T, kJacobi><<<g, 256, 0, s>>>((const C*)coef, n[0], n[1], n[2], (const C*)x,
+                                                     (const C*)b, (C*)y, R, (T)omega_j);
+      break;
+    case kJacobi0:
+      stored_stencil_k<T, kJacobi0><<<g, 256, 0, s>>>((const C*)coef, n[0], n[1], n[2], (const C*)x,
+                                                      (const C*)b, (C*)y, R, (T)omega_j);
+      break;
+    default:
+      return cudaErrorInvalidValue;
+  }
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+#define HX_GAL_INST(T)                                                                             \
+  template cudaError_t launch_galerkin_onfly<T>(const OpDesc<T>&, void*, const int*, cudaStream_t); \
+  template cudaError_t launch_galerkin_stored<T>(const void*, const int*, void*, const int*,       \
+                                                 cudaStream_t);                                    \
+  template cudaError_t launch_stored_stencil<T>(const void*, const int*, int, const void*,         \
+                                                const void*, void*, int, double, cudaStream_t);
+HX_GAL_INST(float)
+HX_GAL_INST(double)
+
+}  // namespace hx

@@ -21,6 +21,7 @@
 
 #include "hx_complex.cuh"
 #include "hx_context.h"
+#include "hx_galerkin.cuh"
 #include "hx_internal.h"
 #include "hx_vec.cuh"
 
@@ -53,9 +54,12 @@ struct SolverImpl : Solver {
   int n[kMaxLev][3];
   long long N[kMaxLev];
   std::string op_key;
-  std::unique_ptr<Level> lvl[kMaxLev];
+  std::unique_ptr<Level> lvl[kMaxLev];  // preconditioner levels (capped PML)
+  std::unique_ptr<Level> lvlA;          // the true fine-level operator
   DevBuf vlev[kMaxLev];                 // coarse velocities (level >= 1)
   DevBuf mb[kMaxLev], me[kMaxLev], mw[kMaxLev];
+  DevBuf acoef[kMaxLev];                // Galerkin coarse operators [27][N_l] (level >= 1)
+  bool galerkin = false;
   // Krylov vectors (inner precision), R * N[0] complex each
   DevBuf r, rhat, p, v, s, t, x, ph, sh, tmp;
   DevBuf r64;                           // FP64 residual (mixed mode)
@@ -159,6 +163,8 @@ class Run {
   cudaError_t stencil(int l, const OpDesc<T>& op, int mode, const void* x, const void* b, void* y,
                       double om) {
     const long long N = S->N[l];
+    if (l > 0 && S->galerkin)
+      return launch_stored_stencil<T>(S->acoef[l].p, S->n[l], mode, x, b, y, S->R, om, stream);
     const bool timed = l == 0 && mode != kJacobi0;
     cudaEvent_t a = timed ? prof_begin(ctx, stream) : nullptr;
     cudaError_t e = launch_stencil(op, mode, x, b, y, S->R, N, om, stream);
@@ -215,7 +221,7 @@ class Run {
     const int R = S->R;
     const long long N = S->N[0];
     const size_t fb = (size_t)R * N * 2 * sizeof(T);
-    const OpDesc<T> A = desc<T>(0, 0.0);
+    const OpDesc<T> A = make_desc<T>(ctx, *S->lvlA, v_fine, 0.0);   // the true operator
     void* r = S->r.p;
     void* rhat = S->rhat.p;
     void* p = S->p.p;
@@ -309,15 +315,17 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->inner_tol = 1e-4;
   o->max_outer = 12;
   o->max_iter = 2000;
-  o->shift_beta = 0.5;
+  o->shift_beta = 1.0;
   o->mg_levels = 0;
-  o->nu_pre = 1;
-  o->nu_post = 1;
+  o->nu_pre = 2;
+  o->nu_post = 2;
   o->coarse_sweeps = 4;
-  o->omega_jacobi = 0.7;
+  o->omega_jacobi = 0.6;
   o->source_spread = 0;
   o->initial_guess = 0;
   o->check_every = 1;
+  o->coarse_galerkin = 0;
+  o->pml_cap = 1.0;
 }
 
 namespace {
@@ -361,25 +369,51 @@ int setup_coarse_inverse(hx_ctx* ctx, SolverImpl* S, const float* /*v_fine*/, do
     S->have_cinv = false;
     return HX_OK;
   }
-  std::vector<float> vc(Nc);
-  const float* vdev = (const float*)S->vlev[L].p;
-  cudaError_t e = cudaMemcpyAsync(vc.data(), vdev, Nc * sizeof(float), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "coarsest velocity");
+  // h[i*54 + 2k (+1)]: coefficient k of row i of the coarsest operator, FP64
+  std::vector<double> h((size_t)Nc * 54);
+  cudaError_t e = cudaSuccess;
+  std::vector<float> vc;
+  if (S->galerkin) {
+    // stored Galerkin operator [27][Nc] in the inner precision
+    const size_t cs = S->prec == 64 ? 16 : 8;
+    std::vector<unsigned char> raw((size_t)27 * Nc * cs);
+    e = cudaMemcpyAsync(raw.data(), S->acoef[L].p, raw.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "coarsest operator");
+    for (long long i = 0; i < Nc; ++i)
+      for (int k = 0; k < 27; ++k) {
+        const size_t q = (size_t)k * Nc + i;
+        if (cs == 16) {
+          h[i * 54 + 2 * k] = ((const double*)raw.data())[2 * q];
+          h[i * 54 + 2 * k + 1] = ((const double*)raw.data())[2 * q + 1];
+        } else {
+          h[i * 54 + 2 * k] = ((const float*)raw.data())[2 * q];
+          h[i * 54 + 2 * k + 1] = ((const float*)raw.data())[2 * q + 1];
+        }
+      }
+    vc.assign((const float*)h.data(), (const float*)(h.data() + h.size()));   // cache key: the operator
+  } else {
+    vc.resize(Nc);
+    const float* vdev = (const float*)S->vlev[L].p;
+    e = cudaMemcpyAsync(vc.data(), vdev, Nc * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "coarsest velocity");
+  }
   char kb[64];
-  std::snprintf(kb, sizeof(kb), " b%.17g p%d", beta, S->prec);
+  std::snprintf(kb, sizeof(kb), " b%.17g p%d g%d", beta, S->prec, S->galerkin ? 1 : 0);
   const std::string key = okey + kb;
   if (S->have_cinv && key == S->cinv_key && vc == S->cinv_v) return HX_OK;
   S->have_cinv = false;
-  double* coef = nullptr;
-  e = cudaMalloc(&coef, (size_t)Nc * 54 * sizeof(double));
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse coefficients");
-  std::vector<double> h((size_t)Nc * 54);
-  e = launch_row_coefficients(make_desc<double>(ctx, *S->lvl[L], vdev, beta), coef, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), coef, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(coef);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse coefficients");
+  if (!S->galerkin) {
+    double* coef = nullptr;
+    e = cudaMalloc(&coef, (size_t)Nc * 54 * sizeof(double));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse coefficients");
+    e = launch_row_coefficients(make_desc<double>(ctx, *S->lvl[L], (const float*)S->vlev[L].p, beta), coef, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), coef, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(coef);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse coefficients");
+  }
   typedef std::complex<double> cd;
   const int n = (int)Nc;
   const int nx = S->n[L][0], ny = S->n[L][1], nz = S->n[L][2];
@@ -470,7 +504,8 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   if (!(opt.tol > 0) || !(opt.inner_tol > 0 && opt.inner_tol < 1) || opt.max_iter < 1 ||
       opt.max_outer < 1 || opt.nu_pre < 1 || opt.nu_post < 0 || opt.coarse_sweeps < 1 ||
       !(opt.omega_jacobi > 0 && opt.omega_jacobi < 2) || !(opt.shift_beta >= 0) ||
-      opt.check_every < 1 || opt.mg_levels < 0 || opt.mg_levels > kMaxLev)
+      opt.check_every < 1 || opt.coarse_galerkin < 0 || opt.coarse_galerkin > 1 ||
+      !(opt.pml_cap >= 0) || opt.mg_levels < 0 || opt.mg_levels > kMaxLev)
     return finish(fail(ctx, HX_ERR_ARG, "invalid solve options"));
   std::vector<int> has_src(nrhs, 0);
   for (int k = 0; k < nsrc; ++k) {
@@ -558,17 +593,19 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
     }
   }
   // ---- operator levels (PML arrays depend on h, f, npml, v_ref, r_coef)
-  char okey[256];
-  std::snprintf(okey, sizeof(okey), "%.17g %.17g %d %d %d %d %d %d %.17g %.17g", grid->h, grid->f,
+  char okey[320];
+  std::snprintf(okey, sizeof(okey), "%.17g %.17g %d %d %d %d %d %d %.17g %.17g cap%.17g", grid->h, grid->f,
                 grid->npml[0], grid->npml[1], grid->npml[2], grid->npml[3], grid->npml[4], grid->npml[5],
-                grid->v_ref, grid->r_coef);
+                grid->v_ref, grid->r_coef, opt.pml_cap);
   if (S->op_key != okey) {
-    for (int l = 0; l < S->nlev; ++l) {
+    // private copies, so LRU eviction in the shared cache cannot free them:
+    // lvlA = the true fine operator (Krylov apply, FP64 residual); lvl[l] =
+    // the preconditioner's levels with the PML damping capped at pml_cap.
+    auto own_copy = [&](const int* nl, double hl, double cap, std::unique_ptr<Level>* dst) -> int {
       Level* tmp = nullptr;
-      if ((st = get_level(ctx, grid, S->n[l], grid->h * (double)(1 << l), &tmp))) return finish(st);
-      // private copy so LRU eviction in the shared cache cannot free it
+      int s2 = get_level(ctx, grid, nl, hl, &tmp, cap);
+      if (s2) return s2;
       auto own = std::make_unique<Level>();
-      *own = Level();
       for (int d = 0; d < 3; ++d) {
         own->n[d] = tmp->n[d];
         own->lo[d] = tmp->lo[d];
@@ -578,12 +615,16 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
         if (e == cudaSuccess) e = cudaMalloc(&own->ax32[d], nb32);
         if (e == cudaSuccess) e = cudaMemcpy(own->ax64[d], tmp->ax64[d], nb64, cudaMemcpyDeviceToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(own->ax32[d], tmp->ax32[d], nb32, cudaMemcpyDeviceToDevice);
-        if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "level copy"));
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "level copy");
       }
       own->h = tmp->h;
       own->f = tmp->f;
-      S->lvl[l] = std::move(own);
-    }
+      *dst = std::move(own);
+      return HX_OK;
+    };
+    if ((st = own_copy(S->n[0], grid->h, 0.0, &S->lvlA))) return finish(st);
+    for (int l = 0; l < S->nlev; ++l)
+      if ((st = own_copy(S->n[l], grid->h * (double)(1 << l), opt.pml_cap, &S->lvl[l]))) return finish(st);
     S->op_key = okey;
   }
   // coarse velocities by injection
@@ -591,6 +632,25 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
     const float* vf = l == 1 ? v_dev : (const float*)S->vlev[l - 1].p;
     cudaError_t e = launch_inject_velocity(vf, S->n[l - 1], (float*)S->vlev[l].p, S->n[l], stream);
     if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "velocity injection"));
+  }
+  // Galerkin coarse operators R A P of the shifted operator (inner precision)
+  S->galerkin = opt.coarse_galerkin != 0 && S->nlev > 1;
+  if (S->galerkin) {
+    const size_t cs = prec == 64 ? 16 : 8;
+    for (int l = 1; l < S->nlev; ++l) {
+      cudaError_t e = S->acoef[l].alloc((size_t)27 * S->N[l] * cs);
+      if (e == cudaSuccess) {
+        if (l == 1)
+          e = prec == 64 ? launch_galerkin_onfly<double>(make_desc<double>(ctx, *S->lvl[0], v_dev, opt.shift_beta),
+                                                         S->acoef[1].p, S->n[1], stream)
+                         : launch_galerkin_onfly<float>(make_desc<float>(ctx, *S->lvl[0], v_dev, opt.shift_beta),
+                                                        S->acoef[1].p, S->n[1], stream);
+        else
+          e = prec == 64 ? launch_galerkin_stored<double>(S->acoef[l - 1].p, S->n[l - 1], S->acoef[l].p, S->n[l], stream)
+                         : launch_galerkin_stored<float>(S->acoef[l - 1].p, S->n[l - 1], S->acoef[l].p, S->n[l], stream);
+      }
+      if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "Galerkin coarse operator"));
+    }
   }
   if ((st = setup_coarse_inverse(ctx, S, v_dev, opt.shift_beta, okey, stream))) return finish(st);
   // ---- sources (grid delta or consistent-mass spread), FP64 amplitudes / h^3
@@ -643,7 +703,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   double worst = 0;
   st = HX_OK;
   std::vector<double> sn2(R), rn2(R);
-  const OpDesc<double> A64 = make_desc<double>(ctx, *S->lvl[0], v_dev, 0.0);
+  const OpDesc<double> A64 = make_desc<double>(ctx, *S->lvlA, v_dev, 0.0);
   // Residual r64 = s - A x64 (FP64) and its per-RHS squared norms.
   double2* r64 = (double2*)S->r64.p;
   if (!opt.initial_guess) {

@@ -41,3 +41,49 @@ def test_jacobi_fixed_point():
     for _ in range(200):
         y = MG.jacobi_sweep(A, y, b, 0.8)
     assert np.allclose(y, x, atol=1e-10)
+
+
+def _two_grid_rate(npml, cap=None, n=17, f=5.0, beta=1.0, nu=2, om=0.6):
+    # asymptotic error reduction of damped-Jacobi two-grid cycles with an exact
+    # Galerkin coarse solve on the shifted operator (oracle pieces only)
+    import scipy.sparse.linalg as spl
+    from oracle import operator as O
+    from oracle import pml as PM
+    from oracle import weights as W
+    from paper_2108_08730_gb300 import synth
+    nodes, T = W.fit_table(d_inv_g=0.01)
+    wl = synth.linear_gradient(n=n, npml=npml, f=f)
+    prof = O.profiles_for(wl.shape, wl.h, wl.npml, wl.v_ref, wl.r_coef)
+    if cap is not None:
+        w = 2 * np.pi * f
+        prof = tuple(PM.Profile1D(p.x_lo, p.x_hi, p.len_lo, p.len_hi, min(p.g0_lo, cap * w),
+                                  min(p.g0_hi, cap * w)) for p in prof)
+    A = O.assemble_csr(wl.v, wl.h, wl.f, prof, T, nodes, beta=beta).tocsr()
+    P = MG.prolongation_matrix(wl.shape)
+    R = MG.restriction_matrix(wl.shape)
+    lu = spl.splu((R @ A @ P).tocsc())
+    d = A.diagonal()
+    rng = np.random.default_rng(0)
+    e = rng.normal(size=A.shape[0]) + 1j * rng.normal(size=A.shape[0])
+    rate = 0.0
+    for _ in range(10):
+        r = A @ e
+        x = om * r / d
+        for _ in range(nu - 1):
+            x = x + om * (r - A @ x) / d
+        x = x + P @ lu.solve(R @ (r - A @ x))
+        for _ in range(nu):
+            x = x + om * (r - A @ x) / d
+        e2 = e - x
+        rate = np.linalg.norm(e2) / np.linalg.norm(e)
+        e = e2
+    return rate
+
+
+def test_pml_stretching_breaks_jacobi_two_grid_and_cap_restores_it():
+    # The reason the preconditioner caps its PML damping (gamma/omega <= 1):
+    # without a PML the two-grid cycle contracts; with the full PML
+    # (gamma/omega ~ 5 at the outer edge) it diverges; with the cap it contracts.
+    assert _two_grid_rate(npml=0) < 0.5
+    assert _two_grid_rate(npml=4) > 1.0
+    assert _two_grid_rate(npml=4, cap=1.0) < 0.8
