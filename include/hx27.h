@@ -197,7 +197,7 @@ typedef struct {
   double omega_jacobi;   /* Jacobi damping (default 0.7)                          */
   int source_spread;     /* 0: grid delta (default); 1: consistent-mass spread    */
   int initial_guess;     /* 1: wavefield_dev holds the starting iterate           */
-  int check_every;       /* iterations between host convergence checks (1)       */
+  int check_every;       /* iterations between host convergence checks (2)       */
   int coarse_galerkin;   /* 1: coarse operators R A P (Galerkin); 0 (default):
                             the stencil rediscretised at 2^l h                    */
   double pml_cap;        /* the preconditioner's PML damping is capped at
@@ -206,6 +206,10 @@ typedef struct {
                             one axis's coefficients far from the others; the
                             preconditioner only has to approximate A^-1, and the
                             Krylov operator keeps the true PML.                   */
+  int use_graphs;        /* 1 (default): each block of check_every Krylov
+                            iterations is captured once per call as a CUDA graph
+                            and replayed (not while hx_profile timing is on);
+                            0: direct launches                                    */
 } hx_solve_opts;
 
 typedef struct {
@@ -235,7 +239,10 @@ enum {
  * launch is bracketed by a CUDA event pair on the solve's stream and its
  * duration, launch count and algorithmic bytes (x, b read + y written once,
  * v read once: (8|16) * (2|3) * N * nrhs + 4 N) are accumulated; read them
- * with hx_profile_read.  Also counts every kernel the library launches. */
+ * with hx_profile_read.  Also counts every kernel the library launches.
+ * While timing is on, hx_solve launches kernels directly instead of replaying
+ * CUDA graphs.  enable = 0 resets the counters and turns timing off (the
+ * launch count of kind -1 keeps counting). */
 int hx_profile(hx_ctx* ctx, int enable);
 
 /* kind in [0, HX_PROF_KINDS): launches, summed duration (ms) and summed

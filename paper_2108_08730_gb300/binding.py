@@ -55,7 +55,7 @@ class hx_solve_opts(C.Structure):
                 ("mg_levels", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("coarse_sweeps", C.c_int), ("omega_jacobi", C.c_double),
                 ("source_spread", C.c_int), ("initial_guess", C.c_int), ("check_every", C.c_int),
-                ("coarse_galerkin", C.c_int), ("pml_cap", C.c_double)]
+                ("coarse_galerkin", C.c_int), ("pml_cap", C.c_double), ("use_graphs", C.c_int)]
 
 
 class hx_solve_report(C.Structure):

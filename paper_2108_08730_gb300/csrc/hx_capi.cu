@@ -215,6 +215,9 @@ hx_ctx::~hx_ctx() {
   for (auto e : prof_pool) cudaEventDestroy(e);
   solvers.clear();
   levels.clear();
+  if (work_stream) cudaStreamDestroy(work_stream);
+  for (auto e : order_ev)
+    if (e) cudaEventDestroy(e);
   if (tab64) cudaFree(tab64);
   if (tab32) cudaFree(tab32);
 }

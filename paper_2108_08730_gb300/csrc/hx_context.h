@@ -52,6 +52,9 @@ struct hx_ctx {
   std::list<std::string> lru;
   std::map<std::string, std::unique_ptr<hx::Solver>> solvers;
   std::list<std::string> solver_lru;
+  // stream the solver runs on, and the events ordering it with the caller's
+  cudaStream_t work_stream = nullptr;
+  cudaEvent_t order_ev[2] = {nullptr, nullptr};
   // profiler (hx_profile): per-class launch count, time, algorithmic bytes
   bool prof_on = false;
   long long prof_launch_base = 0;

@@ -77,6 +77,27 @@ struct SolverImpl : Solver {
   double2 *rho, *rho_new, *alpha, *omega, *beta, *rv, *ts;
   double *tt, *rn2, *bn2, *scale;
   int *active, *brk;
+  // pinned host mirrors read at convergence checks
+  double* pin_rn2 = nullptr;
+  int* pin_act = nullptr;
+  int* pin_act_up = nullptr;
+  // graph of one block of Krylov iterations (rebuilt once per hx_solve call)
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_ready = false;
+  int graph_k = 0;
+  long long graph_kernels = 0;
+  std::vector<hx_ctx::ProfPending> graph_prof;
+
+  ~SolverImpl() override {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto& e : graph_prof) {
+      cudaEventDestroy(e.a);
+      cudaEventDestroy(e.b);
+    }
+    if (pin_rn2) cudaFreeHost(pin_rn2);
+    if (pin_act) cudaFreeHost(pin_act);
+    if (pin_act_up) cudaFreeHost(pin_act_up);
+  }
 };
 
 #define HX_CK(expr)                                          \
@@ -177,40 +198,143 @@ class Run {
     return e;
   }
 
-  // One V-cycle on level l for rhs b; e, w are the level's two work buffers.
-  // Returns the buffer holding the result (e or w).
+  // One V-cycle on level l for rhs b; the result is left in e (w is the
+  // level's second work buffer).  The Jacobi sweeps ping-pong between e and
+  // w; the starting buffer is chosen by the parity of the sweep count so that
+  // the last sweep writes e, which keeps every launch's pointers fixed from
+  // one Krylov iteration to the next (a requirement of graph replay).
   template <typename T>
-  int vcycle(int l, const void* b, void* e, void* w, void** out) {
+  int vcycle(int l, const void* b, void* e, void* w) {
     const OpDesc<T> op = desc<T>(l, opt.shift_beta);
     const long long N = S->N[l];
     const int R = S->R;
-    void* cur = e;
-    void* oth = w;
-    if (l == S->nlev - 1 && S->have_cinv) {
-      HX_CK(launch_dense_matvec<T>(S->cinv.p, b, cur, N, R, stream));
-      *out = cur;
+    const bool coarsest = l == S->nlev - 1;
+    if (coarsest && S->have_cinv) {
+      HX_CK(launch_dense_matvec<T>(S->cinv.p, b, e, N, R, stream));
       return HX_OK;
     }
+    const int pre = coarsest ? opt.coarse_sweeps : opt.nu_pre;
+    const int swaps = (pre - 1) + (coarsest ? 0 : opt.nu_post);
+    void* cur = swaps % 2 == 0 ? e : w;
+    void* oth = swaps % 2 == 0 ? w : e;
     HX_CK(stencil<T>(l, op, kJacobi0, nullptr, b, cur, opt.omega_jacobi));
-    const int pre = (l == S->nlev - 1) ? opt.coarse_sweeps : opt.nu_pre;
     for (int k = 1; k < pre; ++k) {
       HX_CK(stencil<T>(l, op, kJacobi, cur, b, oth, opt.omega_jacobi));
       std::swap(cur, oth);
     }
-    if (l < S->nlev - 1) {
+    if (!coarsest) {
       HX_CK(stencil<T>(l, op, kResidual, cur, b, oth, 0.0));
       HX_CK(launch_restrict<T>(oth, S->n[l], S->mb[l + 1].p, S->n[l + 1], R, stream));
-      void* ec = nullptr;
-      int st = vcycle<T>(l + 1, S->mb[l + 1].p, S->me[l + 1].p, S->mw[l + 1].p, &ec);
+      int st = vcycle<T>(l + 1, S->mb[l + 1].p, S->me[l + 1].p, S->mw[l + 1].p);
       if (st) return st;
-      HX_CK(launch_prolong_add<T>(cur, S->n[l], ec, S->n[l + 1], R, stream));
+      HX_CK(launch_prolong_add<T>(cur, S->n[l], S->me[l + 1].p, S->n[l + 1], R, stream));
       for (int k = 0; k < opt.nu_post; ++k) {
         HX_CK(stencil<T>(l, op, kJacobi, cur, b, oth, opt.omega_jacobi));
         std::swap(cur, oth);
       }
     }
-    *out = cur;
+    return cur == e ? HX_OK : fail(ctx, HX_ERR_STATE, "V-cycle buffer parity");
+  }
+
+  // One BiCGStab iteration (all RHS), launches only.
+  template <typename T>
+  int bicg_iteration(const OpDesc<T>& A) {
+    const int R = S->R;
+    const long long N = S->N[0];
+    double2* part = (double2*)S->part.p;
+    HX_CK(launch_dot<T>(S->rhat.p, S->r.p, N, R, part, S->rho_new, stream));
+    HX_CK(launch_scal_beta(S->beta, S->rho, S->rho_new, S->alpha, S->omega, S->active, S->brk, R, stream));
+    HX_CK(launch_bicg_p<T>(S->p.p, S->r.p, S->v.p, S->beta, S->omega, N, R, stream));
+    int st = vcycle<T>(0, S->p.p, S->ph.p, S->tmp.p);
+    if (st) return st;
+    HX_CK(stencil<T>(0, A, kApply, S->ph.p, nullptr, S->v.p, 0.0));
+    HX_CK(launch_dot<T>(S->rhat.p, S->v.p, N, R, part, S->rv, stream));
+    HX_CK(launch_scal_alpha(S->alpha, S->rho, S->rv, S->active, S->brk, R, stream));
+    HX_CK(launch_bicg_s<T>(S->s.p, S->r.p, S->v.p, S->alpha, N, R, stream));
+    st = vcycle<T>(0, S->s.p, S->sh.p, S->tmp.p);
+    if (st) return st;
+    HX_CK(stencil<T>(0, A, kApply, S->sh.p, nullptr, S->t.p, 0.0));
+    HX_CK(launch_dot<T>(S->t.p, S->s.p, N, R, part, S->ts, stream));
+    HX_CK(launch_norm2<T>(S->t.p, N, R, part, S->tt, stream));
+    HX_CK(launch_scal_omega(S->omega, S->ts, S->tt, S->active, S->brk, R, stream));
+    HX_CK(launch_bicg_xr<T>(S->x.p, S->r.p, S->s.p, S->ph.p, S->sh.p, S->t.p, S->alpha, S->omega, N, R, stream));
     return HX_OK;
+  }
+
+  // k iterations followed by the residual norms and active flags copied to
+  // pinned host memory: the unit replayed between host convergence checks.
+  template <typename T>
+  int bicg_block(const OpDesc<T>& A, int k) {
+    for (int j = 0; j < k; ++j) {
+      int st = bicg_iteration<T>(A);
+      if (st) return st;
+    }
+    const int R = S->R;
+    HX_CK(launch_norm2<T>(S->r.p, S->N[0], R, (double2*)S->part.p, S->rn2, stream));
+    HX_CK(cudaMemcpyAsync(S->pin_rn2, S->rn2, R * sizeof(double), cudaMemcpyDeviceToHost, stream));
+    HX_CK(cudaMemcpyAsync(S->pin_act, S->active, R * sizeof(int), cudaMemcpyDeviceToHost, stream));
+    return HX_OK;
+  }
+
+  // Capture bicg_block as a CUDA graph (instantiated once per hx_solve call,
+  // updated in place when the topology is unchanged).  Returns false when
+  // capture is unavailable; the caller then launches directly.
+  template <typename T>
+  bool capture_block(const OpDesc<T>& A, int k) {
+    if (S->graph_ready && S->graph_k == k) return true;
+    if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return false;
+    const size_t p0 = ctx->prof_pending.size();
+    const long long c0 = launch_count();
+    const int st = bicg_block<T>(A, k);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(stream, &g);
+    // kernels captured, not run: count them per replay instead
+    S->graph_kernels = launch_count() - c0;
+    count_launch(-(int)S->graph_kernels);
+    // event pairs recorded inside the graph belong to it, not to the pending list
+    for (auto& e : S->graph_prof) {
+      ctx->prof_pool.push_back(e.a);
+      ctx->prof_pool.push_back(e.b);
+    }
+    S->graph_prof.assign(ctx->prof_pending.begin() + p0, ctx->prof_pending.end());
+    ctx->prof_pending.resize(p0);
+    if (st || ec != cudaSuccess || !g) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return false;
+    }
+    bool ok = false;
+    if (S->gexec) {
+      cudaGraphExecUpdateResultInfo info;
+      ok = cudaGraphExecUpdate(S->gexec, g, &info) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        cudaGraphExecDestroy(S->gexec);
+        S->gexec = nullptr;
+      }
+    }
+    if (!ok) ok = cudaGraphInstantiate(&S->gexec, g, 0) == cudaSuccess;
+    cudaGraphDestroy(g);
+    if (!ok) {
+      cudaGetLastError();
+      S->gexec = nullptr;
+      return false;
+    }
+    S->graph_ready = true;
+    S->graph_k = k;
+    return true;
+  }
+
+  void collect_graph_prof() {
+    if (!ctx->prof_on) return;
+    for (auto& p : S->graph_prof) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        ctx->prof[p.kind].launches += 1;
+        ctx->prof[p.kind].ms += ms;
+        ctx->prof[p.kind].bytes += p.bytes;
+      }
+    }
   }
 
   // Right-preconditioned BiCGStab on A x = b with x0 = 0.  The RHS b is in
@@ -246,50 +370,34 @@ class Run {
     for (int k = 0; k < R; ++k)
       if (!(S->h_bn2[k] > 0)) S->h_active[k] = 0;
     HX_CK(cudaMemcpyAsync(S->active, S->h_active.data(), R * sizeof(int), cudaMemcpyHostToDevice, stream));
+    (void)p; (void)v; (void)sv; (void)t; (void)ph; (void)sh; (void)tmp;
     int it = 0;
     bool any = false;
     for (int k = 0; k < R; ++k) any = any || S->h_active[k];
+    const int kblk = opt.check_every;
+    // graph replay is skipped while the profiler times individual launches
+    const bool graphed = opt.use_graphs && !ctx->prof_on && capture_block<T>(A, kblk);
     while (any && it < max_iter) {
-      ++it;
-      HX_CK(launch_dot<T>(rhat, r, N, R, (double2*)S->part.p, S->rho_new, stream));
-      HX_CK(launch_scal_beta(S->beta, S->rho, S->rho_new, S->alpha, S->omega, S->active, S->brk, R, stream));
-      HX_CK(launch_bicg_p<T>(p, r, v, S->beta, S->omega, N, R, stream));
-      void* res = nullptr;
-      int st = vcycle<T>(0, p, ph, tmp, &res);
-      if (st) return st;
-      if (res != ph) std::swap(ph, tmp);
-      HX_CK(stencil<T>(0, A, kApply, ph, nullptr, v, 0.0));
-      HX_CK(launch_dot<T>(rhat, v, N, R, (double2*)S->part.p, S->rv, stream));
-      HX_CK(launch_scal_alpha(S->alpha, S->rho, S->rv, S->active, S->brk, R, stream));
-      HX_CK(launch_bicg_s<T>(sv, r, v, S->alpha, N, R, stream));
-      st = vcycle<T>(0, sv, sh, tmp, &res);
-      if (st) return st;
-      if (res != sh) std::swap(sh, tmp);
-      HX_CK(stencil<T>(0, A, kApply, sh, nullptr, t, 0.0));
-      HX_CK(launch_dot<T>(t, sv, N, R, (double2*)S->part.p, S->ts, stream));
-      HX_CK(launch_norm2<T>(t, N, R, (double2*)S->part.p, S->tt, stream));
-      HX_CK(launch_scal_omega(S->omega, S->ts, S->tt, S->active, S->brk, R, stream));
-      HX_CK(launch_bicg_xr<T>(x, r, sv, ph, sh, t, S->alpha, S->omega, N, R, stream));
-      if (it % opt.check_every == 0 || it == max_iter) {
-        HX_CK(launch_norm2<T>(r, N, R, (double2*)S->part.p, S->rn2, stream));
-        HX_CK(cudaMemcpyAsync(S->h_rn2.data(), S->rn2, R * sizeof(double), cudaMemcpyDeviceToHost, stream));
-        std::vector<int> dev_active(R);
-        HX_CK(cudaMemcpyAsync(dev_active.data(), S->active, R * sizeof(int), cudaMemcpyDeviceToHost, stream));
-        HX_CK(cudaStreamSynchronize(stream));
-        any = false;
-        for (int k = 0; k < R; ++k) {
-          if (!std::isfinite(S->h_rn2[k])) return fail(ctx, HX_ERR_NUMERIC, "non-finite Krylov residual");
-          if (S->h_active[k] && (!dev_active[k] || S->h_rn2[k] <= tol * tol * S->h_bn2[k]))
-            S->h_active[k] = 0;
-          any = any || S->h_active[k];
-        }
-        HX_CK(cudaMemcpyAsync(S->active, S->h_active.data(), R * sizeof(int), cudaMemcpyHostToDevice, stream));
+      if (graphed) {
+        HX_CK(cudaGraphLaunch(S->gexec, stream));
+        count_launch(S->graph_kernels);
+      } else {
+        int st = bicg_block<T>(A, kblk);
+        if (st) return st;
       }
+      it += kblk;
+      HX_CK(cudaStreamSynchronize(stream));
+      if (graphed) collect_graph_prof();
+      any = false;
+      for (int k = 0; k < R; ++k) {
+        const double rn2 = S->pin_rn2[k];
+        if (!std::isfinite(rn2)) return fail(ctx, HX_ERR_NUMERIC, "non-finite Krylov residual");
+        if (S->h_active[k] && (!S->pin_act[k] || rn2 <= tol * tol * S->h_bn2[k])) S->h_active[k] = 0;
+        any = any || S->h_active[k];
+      }
+      for (int k = 0; k < R; ++k) S->pin_act_up[k] = S->h_active[k];
+      HX_CK(cudaMemcpyAsync(S->active, S->pin_act_up, R * sizeof(int), cudaMemcpyHostToDevice, stream));
     }
-    // keep the solution pointer in S->x
-    S->ph.p = ph;
-    S->sh.p = sh;
-    S->tmp.p = tmp;
     *iters = it;
     return HX_OK;
   }
@@ -323,9 +431,10 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->omega_jacobi = 0.6;
   o->source_spread = 0;
   o->initial_guess = 0;
-  o->check_every = 1;
+  o->check_every = 2;
   o->coarse_galerkin = 0;
   o->pml_cap = 1.0;
+  o->use_graphs = 1;
 }
 
 namespace {
@@ -505,7 +614,8 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       opt.max_outer < 1 || opt.nu_pre < 1 || opt.nu_post < 0 || opt.coarse_sweeps < 1 ||
       !(opt.omega_jacobi > 0 && opt.omega_jacobi < 2) || !(opt.shift_beta >= 0) ||
       opt.check_every < 1 || opt.coarse_galerkin < 0 || opt.coarse_galerkin > 1 ||
-      !(opt.pml_cap >= 0) || opt.mg_levels < 0 || opt.mg_levels > kMaxLev)
+      !(opt.pml_cap >= 0) || opt.use_graphs < 0 || opt.use_graphs > 1 || opt.mg_levels < 0 ||
+      opt.mg_levels > kMaxLev)
     return finish(fail(ctx, HX_ERR_ARG, "invalid solve options"));
   std::vector<int> has_src(nrhs, 0);
   for (int k = 0; k < nsrc; ++k) {
@@ -518,7 +628,27 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   for (int k = 0; k < nrhs; ++k)
     if (!has_src[k]) return finish(fail(ctx, HX_ERR_ARG, "every rhs needs at least one source"));
   cudaSetDevice(ctx->device);
-  cudaStream_t stream = (cudaStream_t)stream_v;
+  // The solve runs on the context's own non-blocking stream (graph capture is
+  // not possible on the legacy default stream), ordered after the caller's
+  // stream on entry; the caller's stream waits for it on every exit.
+  const cudaStream_t user_stream = (cudaStream_t)stream_v;
+  if (!ctx->work_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->work_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->order_ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->order_ev[1], cudaEventDisableTiming);
+    if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "work stream"));
+  }
+  cudaStream_t stream = ctx->work_stream;
+  cudaEventRecord(ctx->order_ev[0], user_stream);
+  cudaStreamWaitEvent(stream, ctx->order_ev[0], 0);
+  struct Rejoin {
+    hx_ctx* c;
+    cudaStream_t user, work;
+    ~Rejoin() {
+      cudaEventRecord(c->order_ev[1], work);
+      cudaStreamWaitEvent(user, c->order_ev[1], 0);
+    }
+  } rejoin{ctx, user_stream, stream};
   float vmin = 0, vmax = 0;
   if ((st = validate_velocity(ctx, grid, v_dev, stream, &vmin, &vmax))) return finish(st);
   const double inv_g_max = (ctx->n_g - 1) * ctx->d_inv_g;
@@ -586,6 +716,10 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       S->active = (int*)take(nrhs * 4);
       S->brk = (int*)take(nrhs * 4);
       S->h_rn2.resize(nrhs);
+      if (cudaHostAlloc(&S->pin_rn2, nrhs * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
+          cudaHostAlloc(&S->pin_act, nrhs * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||
+          cudaHostAlloc(&S->pin_act_up, nrhs * sizeof(int), cudaHostAllocDefault) != cudaSuccess)
+        return finish(fail(ctx, HX_ERR_OOM, "pinned host buffers"));
       S->h_bn2.resize(nrhs);
       S->h_active.resize(nrhs);
       ctx->solvers[key] = std::move(up);
@@ -695,6 +829,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "setup"));
   auto t_setup = std::chrono::steady_clock::now();
 
+  S->graph_ready = false;   // kernel parameters may differ from the last call
   Run run(ctx, S, grid, v_dev, opt, stream);
   const int R = nrhs;
   double2* x64 = (double2*)wavefield_dev;
