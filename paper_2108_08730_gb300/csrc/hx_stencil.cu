@@ -40,9 +40,28 @@ struct PointW {
   T m;       // omega^2 / v^2
 };
 
+// 4-wide read-only loads of table entries (a node is 12 entries = 3 x 4)
+__device__ __forceinline__ void ld4(const float* p, float* o) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double* o) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p + 2));
+  o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
+// Table position of a row: node i0 and fraction t of 1/G = f h / v.
 template <typename T>
-__device__ __forceinline__ PointW<T> point_weights(const OpDesc<T>& op, const T* tab, float vv) {
-  PointW<T> p;
+struct TabPos {
+  const T* a;   // node i0 (node i0 + 1 follows at a + kTabW)
+  T t;
+  T m;          // omega^2 / v^2
+};
+
+template <typename T>
+__device__ __forceinline__ TabPos<T> tab_pos(const OpDesc<T>& op, const T* tab, float vv) {
+  TabPos<T> q;
   const T vt = (T)vv;
   const T iv = (T)1 / vt;
   T u = op.u_scale * iv;
@@ -50,14 +69,33 @@ __device__ __forceinline__ PointW<T> point_weights(const OpDesc<T>& op, const T*
   u = u < (T)0 ? (T)0 : (u > umax ? umax : u);
   int i0 = (int)u;
   if (i0 > op.n_g - 2) i0 = op.n_g - 2;
-  const T t = u - (T)i0;
-  const T* a = tab + (size_t)i0 * kTabW;
+  q.t = u - (T)i0;
+  q.a = tab + (size_t)i0 * kTabW;
+  q.m = op.omega2 * iv * iv;
+  return q;
+}
+
+// entries [4g, 4g+4) of the interpolated row weights
+template <typename T>
+__device__ __forceinline__ void tab_lerp4(const TabPos<T>& q, int g, T* w) {
+  T lo[4], hi[4];
+  ld4(q.a + 4 * g, lo);
+  ld4(q.a + kTabW + 4 * g, hi);
 #pragma unroll
-  for (int k = 0; k < 11; ++k) {
-    const T lo = a[k], hi = a[kTabW + k];
-    p.w[k] = fma(t, hi - lo, lo);
-  }
-  p.m = op.omega2 * iv * iv;
+  for (int k = 0; k < 4; ++k) w[k] = fma(q.t, hi[k] - lo[k], lo[k]);
+}
+
+template <typename T>
+__device__ __forceinline__ PointW<T> point_weights(const OpDesc<T>& op, const T* tab, float vv) {
+  PointW<T> p;
+  const TabPos<T> q = tab_pos(op, tab, vv);
+  T w12[12];
+  tab_lerp4(q, 0, w12);
+  tab_lerp4(q, 1, w12 + 4);
+  tab_lerp4(q, 2, w12 + 8);
+#pragma unroll
+  for (int k = 0; k < 11; ++k) p.w[k] = w12[k];
+  p.m = q.m;
   return p;
 }
 
@@ -72,26 +110,28 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-constexpr int kTX = 32, kTY = 8, kNSlot = 6, kDist = kNSlot - 3;
+constexpr int kTX = 16, kTY = 16, kNSlot = 6, kDist = kNSlot - 3;
+constexpr int kPW = kTX + 2, kPH = kTY + 2, kPlane = kPW * kPH;   // ring plane (tile + halo)
+constexpr int kLoadIters = (kPlane + kTX * kTY - 1) / (kTX * kTY);
 
 template <typename T, int RB>
 __host__ __device__ constexpr size_t ring_bytes() {
-  return (size_t)kNSlot * RB * (kTY + 2) * (kTX + 2) * sizeof(typename CT<T>::type);
+  return (size_t)kNSlot * RB * kPlane * sizeof(typename CT<T>::type);
 }
+
+__device__ __forceinline__ int next_slot(int s) { return s + 1 == kNSlot ? 0 : s + 1; }
 
 template <typename T, int MODE, bool SHIFT, int RB>
 __global__ void __launch_bounds__(kTX * kTY, sizeof(T) == 4 ? 3 : 2)
 stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
                const typename CT<T>::type* __restrict__ b, typename CT<T>::type* __restrict__ y,
-               int nrhs, long long rstride, int zchunk, T omega_j, int tab_in_smem) {
+               int nrhs, long long rstride, int zchunk, T omega_j) {
   using C = typename CT<T>::type;
-  constexpr int TX = kTX, TY = kTY, PW = TX + 2, PH = TY + 2;
+  constexpr int TX = kTX, TY = kTY, PW = kPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* ring = reinterpret_cast<C*>(smem_raw);                        // [NSLOT][RB][PH][PW]
-  T* tab_s = reinterpret_cast<T*>(smem_raw + ring_bytes<T, RB>());
-  auto R = [&](int slot, int r, int ly, int lx) -> C& {
-    return ring[((slot * RB + r) * PH + ly) * PW + lx];
-  };
+  // this thread's 3x3 window in (slot, rhs) plane: element (dy, dx) at [dy * PW + dx]
+  auto P = [&](int slot, int r) -> const C* { return ring + (slot * RB + r) * kPlane + threadIdx.y * PW + threadIdx.x; };
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int gx0 = blockIdx.x * TX, gy0 = blockIdx.y * TY;
@@ -103,56 +143,64 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
   const int z0 = zc * zchunk, z1 = min(op.nz, z0 + zchunk);
   const bool active = ix < op.nx && iy < op.ny;
   const long long plane = (long long)op.nx * op.ny;
-
-  // stage the derived table (or read it from global memory when too large)
   const T* tab = op.tab;
-  if (tab_in_smem) {
-    for (int i = tid; i < op.n_g * kTabW; i += TX * TY) tab_s[i] = op.tab[i];
-    tab = tab_s;
-  }
 
+  // loader descriptors, fixed for the CTA: the ring elements this thread
+  // copies, their offsets inside a z-plane, and whether they lie in the grid
+  int ld_s[kLoadIters];
+  int ld_g[kLoadIters];
+  bool ld_ok[kLoadIters];
+#pragma unroll
+  for (int k = 0; k < kLoadIters; ++k) {
+    const int e = tid + k * TX * TY;
+    const int ly = e / PW, lx = e - ly * PW;
+    const int gx = gx0 + lx - 1, gy = gy0 + ly - 1;
+    ld_s[k] = e < kPlane ? e : -1;
+    ld_ok[k] = e < kPlane && gx >= 0 && gx < op.nx && gy >= 0 && gy < op.ny;
+    ld_g[k] = ld_ok[k] ? gy * op.nx + gx : 0;
+  }
   // issue the asynchronous copies of plane z (all RB fields) into slot
-  auto issue_plane = [&](int z) {
+  auto issue_plane = [&](int z, int slot) {
     if (z < z0 - 1 || z > z1) return;                     // not needed by this CTA
-    const int slot = (z - z0 + 1) % kNSlot;
     const bool zin = z >= 0 && z < op.nz;
-    for (int e = tid; e < PH * PW; e += TX * TY) {
-      const int ly = e / PW, lx = e - ly * PW;
-      const int gx = gx0 + lx - 1, gy = gy0 + ly - 1;
-      const bool ok = zin && gx >= 0 && gx < op.nx && gy >= 0 && gy < op.ny;
-      const long long off = ok ? (long long)z * plane + (long long)gy * op.nx + gx : 0;
+    const long long zoff = zin ? (long long)z * plane : 0;
+#pragma unroll
+    for (int k = 0; k < kLoadIters; ++k) {
+      if (ld_s[k] < 0) continue;
 #pragma unroll
       for (int r = 0; r < RB; ++r) {
-        const bool okr = ok && r < rcount;
-        const C* src = x + (okr ? (long long)(r0 + r) * rstride + off : 0);
-        cp_async(&R(slot, r, ly, lx), src, (int)sizeof(C), okr);
+        const bool ok = zin && ld_ok[k] && r < rcount;
+        const C* src = x + (ok ? (long long)(r0 + r) * rstride + zoff + ld_g[k] : 0);
+        cp_async(ring + (slot * RB + r) * kPlane + ld_s[k], src, (int)sizeof(C), ok);
       }
     }
   };
 
   // in-plane class sums of column (tx, ty): centre, 4 faces, 4 corners
   C cs[3][RB], es[3][RB], ks[3][RB];   // window: 0 -> z-1, 1 -> z, 2 -> z+1
-  auto plane_sums = [&](int z, int w) {
-    const int slot = (z - z0 + 1) % kNSlot;
+  auto plane_sums = [&](int slot, int w) {
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      cs[w][r] = R(slot, r, ty + 1, tx + 1);
-      es[w][r] = cadd(cadd(R(slot, r, ty + 1, tx), R(slot, r, ty + 1, tx + 2)),
-                      cadd(R(slot, r, ty, tx + 1), R(slot, r, ty + 2, tx + 1)));
-      ks[w][r] = cadd(cadd(R(slot, r, ty, tx), R(slot, r, ty, tx + 2)),
-                      cadd(R(slot, r, ty + 2, tx), R(slot, r, ty + 2, tx + 2)));
+      const C* q = P(slot, r);
+      cs[w][r] = q[PW + 1];
+      es[w][r] = cadd(cadd(q[PW], q[PW + 2]), cadd(q[1], q[2 * PW + 1]));
+      ks[w][r] = cadd(cadd(q[0], q[2]), cadd(q[2 * PW], q[2 * PW + 2]));
     }
   };
 
-  // prologue: planes z0-1 .. z0+kDist in flight, one commit group per plane
+  // prologue: planes z0-1 .. z0+kDist in flight (slots 0..kDist+1), one
+  // commit group per plane
+#pragma unroll
   for (int k = -1; k <= kDist; ++k) {
-    issue_plane(z0 + k);
+    issue_plane(z0 + k, k + 1);
     cp_commit();
   }
   cp_wait<kDist>();                // planes z0-1 and z0 have landed
   __syncthreads();
-  plane_sums(z0 - 1, 0);
-  plane_sums(z0, 1);
+  // rolling slots of planes z-1, z, z+1 and of the plane issued next
+  int s_m = 0, s_0 = 1, s_p = 2, s_issue = kDist + 2;
+  plane_sums(s_m, 0);
+  plane_sums(s_0, 1);
 
   const bool plain_x = ix >= op.plain_lo[0] && ix <= op.plain_hi[0];
   const bool plain_y = iy >= op.plain_lo[1] && iy <= op.plain_hi[1];
@@ -162,31 +210,51 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
   for (int z = z0; z < z1; ++z) {
     cp_wait<kDist - 1>();          // plane z+1 has landed (own copies)
     __syncthreads();               // ... for every thread; step z-1 finished everywhere
-    issue_plane(z + kDist + 1);    // into the slot of plane z-2
+    issue_plane(z + kDist + 1, s_issue);   // into the slot of plane z-2
     cp_commit();
-    plane_sums(z + 1, 2);
+    plane_sums(s_p, 2);
 
     const float vv = v_next;
     if (active && z + 1 < z1) v_next = __ldg(op.v + (long long)(z + 1) * plane + (long long)iy * op.nx + ix);
 
     if (active) {
       const long long off = (long long)z * plane + (long long)iy * op.nx + ix;
-      const PointW<T> pw = point_weights(op, tab, vv);
-      const T m = pw.m;
+      // interpolated row weights: wv[0..3] stiffness class coefficients x h^2,
+      // wv[4..7] mass weights, wv[8..10] transverse weights (PML rows only)
+      const TabPos<T> tq = tab_pos(op, tab, vv);
+      T wv[12];
+      tab_lerp4(tq, 0, wv);
+      tab_lerp4(tq, 1, wv + 4);
+      const T m = tq.m;
       const bool plain_z = z >= op.plain_lo[2] && z <= op.plain_hi[2];
-      if (plain_xy) {
-        // interior-like row: class form, plus z-stretching corrections
+      if (plain_x || plain_y) {
+        // At most one of x, y stretched: the interior class form plus, for each
+        // stretched axis d, (up_d - 1/h^2)(F_d+ - F_d0) + (dn_d - 1/h^2)(F_d- - F_d0)
+        // with F_d(s) the transverse average at offset s along d (z from the
+        // register window, x or y from the ring).
         T a[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a[k] = fma(m, pw.w[4 + k], pw.w[k] * op.inv_h2);
-        C diag = cmk(a[0], SHIFT ? op.beta * m * pw.w[4] : (T)0);
-        C duz = czero<C>(), ddz = czero<C>();
+        for (int k = 0; k < 4; ++k) a[k] = fma(m, wv[4 + k], wv[k] * op.inv_h2);
+        C diag = cmk(a[0], SHIFT ? op.beta * m * wv[4] : (T)0);
+        C duz = czero<C>(), ddz = czero<C>(), dua = czero<C>(), dda = czero<C>();
+        if (!plain_z || !plain_xy) tab_lerp4(tq, 2, wv + 8);
         if (!plain_z) {
           const T* q = op.axis[2] + 4 * (size_t)z;
           duz = cmk(ldg(q) - op.inv_h2, ldg(q + 1));
           ddz = cmk(ldg(q + 2) - op.inv_h2, ldg(q + 3));
-          diag = csub(diag, cscale(pw.w[8], cadd(duz, ddz)));
+          diag = csub(diag, cscale(wv[8], cadd(duz, ddz)));
         }
+        // the stretched in-plane axis (if any): x when !plain_x, else y
+        const int ax = plain_x ? 1 : 0;
+        if (!plain_xy) {
+          const T* q = (ax == 0 ? op.axis[0] + 4 * (size_t)ix : op.axis[1] + 4 * (size_t)iy);
+          dua = cmk(ldg(q) - op.inv_h2, ldg(q + 1));
+          dda = cmk(ldg(q + 2) - op.inv_h2, ldg(q + 3));
+          diag = csub(diag, cscale(wv[8], cadd(dua, dda)));
+        }
+        // ring offsets of the line along the stretched axis and its transverse pair
+        const int stx = ax == 0 ? 1 : 0, sty = 1 - stx;      // step along the axis
+        const int ptx = sty, pty = stx;                      // step to the pair
         C dinv = czero<C>();
         if (MODE == kJacobi) dinv = cscale(omega_j, crcp(diag));
 #pragma unroll
@@ -200,20 +268,40 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
           acc = cfmar(a[2], e12, acc);
           acc = cfmar(a[3], c8, acc);
           if (SHIFT) {
-            C ms = cscale(pw.w[4], c0);
-            ms = cfmar(pw.w[5], f6, ms);
-            ms = cfmar(pw.w[6], e12, ms);
-            ms = cfmar(pw.w[7], c8, ms);
+            C ms = cscale(wv[4], c0);
+            ms = cfmar(wv[5], f6, ms);
+            ms = cfmar(wv[6], e12, ms);
+            ms = cfmar(wv[7], c8, ms);
             acc = cadd(acc, cscale_i(op.beta * m, ms));
           }
           if (!plain_z) {
             // F_z(s) = t0 c(z+s) + t1 faces(z+s) + t2 corners(z+s)
-            const T t0 = pw.w[8], t1 = pw.w[9], t2 = pw.w[10];
+            const T t0 = wv[8], t1 = wv[9], t2 = wv[10];
             const C fzm = cfmar(t2, ks[0][r], cfmar(t1, es[0][r], cscale(t0, cs[0][r])));
             const C fz0 = cfmar(t2, ks[1][r], cfmar(t1, es[1][r], cscale(t0, cs[1][r])));
             const C fzp = cfmar(t2, ks[2][r], cfmar(t1, es[2][r], cscale(t0, cs[2][r])));
             acc = cfma(duz, csub(fzp, fz0), acc);
             acc = cfma(ddz, csub(fzm, fz0), acc);
+          }
+          if (!plain_xy) {
+            const T t0 = wv[8], t1 = wv[9], t2 = wv[10];
+            C Fm = czero<C>(), F0 = czero<C>(), Fp = czero<C>();
+#pragma unroll
+            for (int dk = -1; dk <= 1; ++dk) {
+              const C* q = P(dk < 0 ? s_m : (dk > 0 ? s_p : s_0), r);
+              const T ta = dk != 0 ? t1 : t0, tb = dk != 0 ? t2 : t1;
+#pragma unroll
+              for (int s = -1; s <= 1; ++s) {
+                const int c = (1 + s * sty) * PW + 1 + s * stx;   // line element at offset s
+                const int pr = pty * PW + ptx;                    // its transverse pair
+                const C f = cfmar(tb, cadd(q[c - pr], q[c + pr]), cscale(ta, q[c]));
+                if (s < 0) Fm = cadd(Fm, f);
+                else if (s == 0) F0 = cadd(F0, f);
+                else Fp = cadd(Fp, f);
+              }
+            }
+            acc = cfma(dua, csub(Fp, F0), acc);
+            acc = cfma(dda, csub(Fm, F0), acc);
           }
           if (r < rcount) {
             const long long o = (long long)(r0 + r) * rstride + off;
@@ -225,7 +313,8 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
         }
       } else {
         // x/y PML row: general form sum_d up_d (F_d+ - F_d0) + dn_d (F_d- - F_d0)
-        const T t0 = pw.w[8], t1 = pw.w[9], t2 = pw.w[10];
+        tab_lerp4(tq, 2, wv + 8);
+        const T t0 = wv[8], t1 = wv[9], t2 = wv[10];
         const int idx[3] = {ix, iy, z};
         C up[3], dn[3];
 #pragma unroll
@@ -236,7 +325,7 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
         }
         const C mc = cmk(m, SHIFT ? op.beta * m : (T)0);   // m (1 + i beta)
         const C sdiag = cadd(cadd(up[0], dn[0]), cadd(cadd(up[1], dn[1]), cadd(up[2], dn[2])));
-        const C diag = cfma(mc, cmk(pw.w[4], (T)0), cscale(-t0, sdiag));
+        const C diag = cfma(mc, cmk(wv[4], (T)0), cscale(-t0, sdiag));
         C dinv = czero<C>();
         if (MODE == kJacobi) dinv = cscale(omega_j, crcp(diag));
         // Streams the three z-planes of the 27-point neighbourhood: Fx[i]
@@ -251,12 +340,12 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
           C acc = czero<C>(), ms = czero<C>(), xc = czero<C>();
 #pragma unroll 1
           for (int dk = -1; dk <= 1; ++dk) {
-            const int slot = (z - z0 + 1 + dk) % kNSlot;
+            const C* qp = P(dk < 0 ? s_m : (dk > 0 ? s_p : s_0), r);
             C q[3][3];
 #pragma unroll
             for (int j = 0; j < 3; ++j)
 #pragma unroll
-              for (int i = 0; i < 3; ++i) q[j][i] = R(slot, r, ty + j, tx + i);
+              for (int i = 0; i < 3; ++i) q[j][i] = qp[j * PW + i];
             const bool off_plane = dk != 0;
             const T ta = off_plane ? t1 : t0;      // transverse weight at in-plane offset 0
             const T tb = off_plane ? t2 : t1;      // ... at in-plane offset 1
@@ -269,9 +358,9 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
             const C tp = cfmar(t2, corners, cfmar(t1, faces, cscale(t0, q[1][1])));
             const C dzk = dk < 0 ? dz_m : (dk > 0 ? dz_p : dz_0);
             acc = cfma(dzk, tp, acc);
-            const T mw0 = off_plane ? pw.w[5] : pw.w[4];
-            const T mw1 = off_plane ? pw.w[6] : pw.w[5];
-            const T mw2 = off_plane ? pw.w[7] : pw.w[6];
+            const T mw0 = off_plane ? wv[5] : wv[4];
+            const T mw1 = off_plane ? wv[6] : wv[5];
+            const T mw2 = off_plane ? wv[7] : wv[6];
             ms = cfmar(mw2, corners, cfmar(mw1, faces, cfmar(mw0, q[1][1], ms)));
             if (!off_plane) xc = q[1][1];
           }
@@ -294,6 +383,10 @@ stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
       cs[0][r] = cs[1][r]; es[0][r] = es[1][r]; ks[0][r] = ks[1][r];
       cs[1][r] = cs[2][r]; es[1][r] = es[2][r]; ks[1][r] = ks[2][r];
     }
+    s_m = next_slot(s_m);
+    s_0 = next_slot(s_0);
+    s_p = next_slot(s_p);
+    s_issue = next_slot(s_issue);
   }
   cp_wait<0>();
 }
@@ -365,12 +458,25 @@ __global__ void row_coef_kernel(OpDesc<double> op, double2* __restrict__ coef) {
   }
 }
 
+// z-range per CTA: minimise (waves of CTAs) x (z-steps per CTA + ring
+// prologue), with waves counted against the resident-CTA slots of 152 SMs.
 int pick_zchunk(int nz, int ntiles_xy, int nrb, int ctas_per_sm) {
-  const int target = 152 * ctas_per_sm * 2;
-  int nzc = (target + ntiles_xy * nrb - 1) / (ntiles_xy * nrb);
-  nzc = nzc < 1 ? 1 : nzc;
-  int zc = (nz + nzc - 1) / nzc;
-  return zc < 8 ? 8 : zc;
+  const long long slots = 152LL * ctas_per_sm;
+  int best = nz;
+  double best_cost = 1e300;
+  for (int zc = nz; zc >= 4; --zc) {
+    const long long nzc = (nz + zc - 1) / zc;
+    if ((nz + nzc - 1) / nzc != zc) continue;          // same split as a larger zc
+    const long long ctas = (long long)ntiles_xy * nrb * nzc;
+    if (nzc * nrb > 65535) break;
+    const long long waves = (ctas + slots - 1) / slots;
+    const double cost = (double)waves * (zc + kDist + 2);
+    if (cost < best_cost * 0.999) {
+      best_cost = cost;
+      best = zc;
+    }
+  }
+  return best;
 }
 
 template <typename T, int MODE, bool SHIFT, int RB>
@@ -379,16 +485,15 @@ cudaError_t launch_t(const OpDesc<T>& op, const void* x, const void* b, void* y,
   using C = typename CT<T>::type;
   const int bx = (op.nx + kTX - 1) / kTX, by = (op.ny + kTY - 1) / kTY;
   const int nrb = (nrhs + RB - 1) / RB;
-  const size_t tab_bytes = (size_t)op.n_g * kTabW * sizeof(T);
-  const int tab_in_smem = tab_bytes <= 48 * 1024 ? 1 : 0;
-  const size_t smem = ring_bytes<T, RB>() + (tab_in_smem ? tab_bytes : 0);
+  // the weight table is read through the read-only cache (staging it per CTA
+  // cost more L2 traffic than the field itself on small grids)
+  const size_t smem = ring_bytes<T, RB>();
   auto kern = stencil_kernel<T, MODE, SHIFT, RB>;
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(ring_bytes<T, RB>() + 48 * 1024));
+  if (smem > 48 * 1024 && (dev < 0 || dev >= 64 || !attr_set[dev])) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) attr_set[dev] = true;
   }
@@ -397,8 +502,7 @@ cudaError_t launch_t(const OpDesc<T>& op, const void* x, const void* b, void* y,
   const long long gz = (long long)nzc * nrb;
   if (gz > 65535) return cudaErrorInvalidConfiguration;
   dim3 grid(bx, by, (unsigned)gz), block(kTX, kTY);
-  kern<<<grid, block, smem, s>>>(op, (const C*)x, (const C*)b, (C*)y, nrhs, rstride, zchunk, (T)omega_j,
-                                 tab_in_smem);
+  kern<<<grid, block, smem, s>>>(op, (const C*)x, (const C*)b, (C*)y, nrhs, rstride, zchunk, (T)omega_j);
   count_launch(1);
   return cudaGetLastError();
 }
