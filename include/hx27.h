@@ -115,6 +115,9 @@ int hx_set_table(hx_ctx* ctx, const double* table_host, int n_g, double d_inv_g)
 
 /* ---------------------------------------------------------------- operator */
 
+/* Flag or-ed into hx_apply_operator's precision argument (see there). */
+#define HX_APPLY_DIRECT 0x100
+
 /* y = A x for nrhs right-hand sides, A the impedance matrix [M + S] of Eq. 3
  * built on the fly per row (Eqs. 4-8 with the GA weight selection): the row's
  * 1/G = f h / v is looked up in the table by linear interpolation (clamped to
@@ -125,7 +128,10 @@ int hx_set_table(hx_ctx* ctx, const double* table_host, int n_g, double d_inv_g)
  * omega^2 by (1 + i shift_beta) omega^2 (the complex-shifted operator of the
  * preconditioner; 0 gives the paper's operator).
  *   precision 32: x, y complex64, arithmetic FP32 (table in FP32);
- *   precision 64: x, y complex128, arithmetic FP64.
+ *   precision 64: x, y complex128, arithmetic FP64;
+ *   | HX_APPLY_DIRECT: use the one-thread-per-row kernel (coefficients formed
+ *   per row, neighbours through the read-only cache) that the multigrid uses
+ *   on small coarse grids, instead of the tiled z-marching kernel.
  *   x_dev, y_dev: [nrhs][nz][ny][nx], must not overlap.
  * Velocities are not validated here (see hx_solve).  Asynchronous on stream.
  * Errors: HX_ERR_ARG, HX_ERR_STATE (no table), HX_ERR_CUDA. */

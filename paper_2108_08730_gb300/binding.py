@@ -26,6 +26,7 @@ EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_
            "hx_assemble_csr_noalloc")
 
 NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
+APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
 
 PROF_KINDS = {"apply32": 0, "smooth32": 1, "apply64": 2, "smooth64": 3}
 
@@ -202,11 +203,14 @@ class Context:
         T = np.ascontiguousarray(table, dtype=np.float64)
         self._check(lib().hx_set_table(self._h, _dptr(T), T.shape[0], float(d_inv_g)), "hx_set_table")
 
-    def apply(self, grid, v, x, y, shift_beta=0.0, stream=None):
+    def apply(self, grid, v, x, y, shift_beta=0.0, stream=None, direct=False):
         """y = A x; v float32 (nz,ny,nx) and x, y complex64/complex128
-        (nrhs, nz, ny, nx) torch CUDA tensors."""
+        (nrhs, nz, ny, nx) torch CUDA tensors.  direct=True selects the
+        one-thread-per-row kernel (HX_APPLY_DIRECT)."""
         import torch
         prec = 32 if x.dtype == torch.complex64 else 64
+        if direct:
+            prec |= APPLY_DIRECT
         nrhs = x.shape[0] if x.dim() == 4 else 1
         self._check(lib().hx_apply_operator(self._h, C.byref(grid), C.c_void_p(v.data_ptr()),
                                             float(shift_beta), C.c_void_p(x.data_ptr()),

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "hx_context.h"
+#include "hx_galerkin.cuh"
 #include "hx_internal.h"
 
 namespace hx {
@@ -306,6 +307,8 @@ int hx_apply_operator(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doub
   if (!ctx->tab64) return fail(ctx, HX_ERR_STATE, "no weight table set (hx_set_table)");
   if (!v_dev || !x_dev || !y_dev || nrhs < 1) return fail(ctx, HX_ERR_ARG, "null buffer or nrhs < 1");
   if (x_dev == y_dev) return fail(ctx, HX_ERR_ARG, "x and y must not overlap");
+  const bool direct = (precision & HX_APPLY_DIRECT) != 0;
+  precision &= ~HX_APPLY_DIRECT;
   if (precision != 32 && precision != 64) return fail(ctx, HX_ERR_ARG, "precision must be 32 or 64");
   if (!std::isfinite(shift_beta)) return fail(ctx, HX_ERR_ARG, "shift_beta must be finite");
   cudaSetDevice(ctx->device);
@@ -315,10 +318,15 @@ int hx_apply_operator(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doub
   const long long N = (long long)grid->nx * grid->ny * grid->nz;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  if (precision == 32)
-    e = launch_stencil(make_desc<float>(ctx, *lv, v_dev, shift_beta), kApply, x_dev, nullptr, y_dev, nrhs, N, 0.0, s);
-  else
-    e = launch_stencil(make_desc<double>(ctx, *lv, v_dev, shift_beta), kApply, x_dev, nullptr, y_dev, nrhs, N, 0.0, s);
+  if (precision == 32) {
+    const OpDesc<float> d = make_desc<float>(ctx, *lv, v_dev, shift_beta);
+    e = direct ? launch_direct_stencil<float>(d, kApply, x_dev, nullptr, y_dev, nrhs, 0.0, s)
+               : launch_stencil(d, kApply, x_dev, nullptr, y_dev, nrhs, N, 0.0, s);
+  } else {
+    const OpDesc<double> d = make_desc<double>(ctx, *lv, v_dev, shift_beta);
+    e = direct ? launch_direct_stencil<double>(d, kApply, x_dev, nullptr, y_dev, nrhs, 0.0, s)
+               : launch_stencil(d, kApply, x_dev, nullptr, y_dev, nrhs, N, 0.0, s);
+  }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "apply launch");
   return HX_OK;
 }

@@ -147,6 +147,46 @@ stored_stencil_k(const typename CT<T>::type* __restrict__ coef, int nx, int ny, 
   }
 }
 
+// Small grids (coarse multigrid levels): one thread per row, the 27
+// coefficients formed on the fly (the same row as the tiled kernel) and the
+// neighbours read through the read-only cache.  A z-marching tiled kernel is
+// latency-bound when a level has only a few tiles.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128)
+direct_stencil_k(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
+                 const typename CT<T>::type* __restrict__ b, typename CT<T>::type* __restrict__ y,
+                 int R, T omega_j) {
+  using C = typename CT<T>::type;
+  const long long N = (long long)op.nx * op.ny * op.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % op.nx), iy = (int)((i / op.nx) % op.ny), iz = (int)(i / ((long long)op.nx * op.ny));
+    C a[27];
+    fine_row<T>(op, ix, iy, iz, a);
+    const C dinv = cscale(omega_j, crcp(a[13]));
+    for (int r = 0; r < R; ++r) {
+      const long long o = (long long)r * N + i;
+      if (MODE == kJacobi0) {
+        y[o] = cmul(dinv, __ldg(b + o));
+        continue;
+      }
+      const C* xr = x + (long long)r * N;
+      C acc = czero<C>();
+#pragma unroll
+      for (int k = 0; k < 27; ++k) {
+        const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dk = k / 9 - 1;
+        const int jx = ix + di, jy = iy + dj, jz = iz + dk;
+        if (jx < 0 || jx >= op.nx || jy < 0 || jy >= op.ny || jz < 0 || jz >= op.nz) continue;
+        acc = cfma(a[k], __ldg(xr + i + di + (long long)op.nx * (dj + (long long)op.ny * dk)), acc);
+      }
+      C res = acc;
+      if (MODE == kResidual) res = b ? csub(__ldg(b + o), acc) : cmk(-acc.x, -acc.y);
+      if (MODE == kJacobi) res = cfma(dinv, csub(__ldg(b + o), acc), __ldg(xr + i));
+      y[o] = res;
+    }
+  }
+}
+
 unsigned blocks_for(long long n, int threads, int cap) {
   long long b = (n + threads - 1) / threads;
   if (b < 1) b = 1;
@@ -208,6 +248,28 @@ cudaError_t launch_stored_stencil(const void* coef, const int n[3], int mode, co
   count_launch(1);
   return cudaGetLastError();
 }
+
+template <typename T>
+cudaError_t launch_direct_stencil(const OpDesc<T>& op, int mode, const void* x, const void* b, void* y,
+                                  int R, double omega_j, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const long long N = (long long)op.nx * op.ny * op.nz;
+  const unsigned g = blocks_for(N, 128, 152 * 32);
+  const T om = (T)omega_j;
+  switch (mode) {
+    case kApply: direct_stencil_k<T, kApply><<<g, 128, 0, s>>>(op, (const C*)x, (const C*)b, (C*)y, R, om); break;
+    case kResidual: direct_stencil_k<T, kResidual><<<g, 128, 0, s>>>(op, (const C*)x, (const C*)b, (C*)y, R, om); break;
+    case kJacobi: direct_stencil_k<T, kJacobi><<<g, 128, 0, s>>>(op, (const C*)x, (const C*)b, (C*)y, R, om); break;
+    case kJacobi0: direct_stencil_k<T, kJacobi0><<<g, 128, 0, s>>>(op, (const C*)x, (const C*)b, (C*)y, R, om); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch(1);
+  return cudaGetLastError();
+}
+template cudaError_t launch_direct_stencil<float>(const OpDesc<float>&, int, const void*, const void*, void*,
+                                                  int, double, cudaStream_t);
+template cudaError_t launch_direct_stencil<double>(const OpDesc<double>&, int, const void*, const void*, void*,
+                                                   int, double, cudaStream_t);
 
 #define HX_GAL_INST(T)                                                                             \
   template cudaError_t launch_galerkin_onfly<T>(const OpDesc<T>&, void*, const int*, cudaStream_t); \

@@ -21,5 +21,10 @@ cudaError_t launch_galerkin_stored(const void* fine_coef, const int nf[3], void*
 template <typename T>
 cudaError_t launch_stored_stencil(const void* coef, const int n[3], int mode, const void* x,
                                   const void* b, void* y, int R, double omega_j, cudaStream_t s);
+// the on-the-fly operator of `op`, one thread per row (for small grids); same
+// modes, R fields of op.nx*op.ny*op.nz each
+template <typename T>
+cudaError_t launch_direct_stencil(const OpDesc<T>& op, int mode, const void* x, const void* b, void* y,
+                                  int R, double omega_j, cudaStream_t s);
 
 }  // namespace hx

@@ -108,6 +108,8 @@ struct SolverImpl : Solver {
 
 // Largest coarsest level solved exactly through a dense inverse.
 constexpr long long kMaxDense = 512;
+// Coarse levels up to this size use the one-thread-per-row stencil kernel.
+constexpr long long kDirectMaxPoints = 300000;
 
 int plan_levels(const int n0[3], int requested, int out[kMaxLev][3]) {
   out[0][0] = n0[0];
@@ -186,6 +188,8 @@ class Run {
     const long long N = S->N[l];
     if (l > 0 && S->galerkin)
       return launch_stored_stencil<T>(S->acoef[l].p, S->n[l], mode, x, b, y, S->R, om, stream);
+    if (l > 0 && N <= kDirectMaxPoints)   // coarse level: a few tiles only
+      return launch_direct_stencil<T>(op, mode, x, b, y, S->R, om, stream);
     const bool timed = l == 0 && mode != kJacobi0;
     cudaEvent_t a = timed ? prof_begin(ctx, stream) : nullptr;
     cudaError_t e = launch_stencil(op, mode, x, b, y, S->R, N, om, stream);

@@ -60,7 +60,8 @@ def _bound_check(A, x, y_gpu, tol):
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("nrhs", [1, 5])
 @pytest.mark.parametrize("beta", [0.0, 0.5])
-def test_apply_matches_oracle_csr(ctx, otable, case, prec, nrhs, beta):
+@pytest.mark.parametrize("direct", [False, True], ids=["tiled", "direct"])
+def test_apply_matches_oracle_csr(ctx, otable, case, prec, nrhs, beta, direct):
     shape, h, f, npml, vmin, vmax = _cases()[case]
     nodes, T = otable
     v = synth.random_velocity(shape, 100 + case, vmin, vmax) if vmin < vmax else \
@@ -73,7 +74,7 @@ def test_apply_matches_oracle_csr(ctx, otable, case, prec, nrhs, beta):
     vd = torch.from_numpy(v).cuda()
     xd = torch.from_numpy(x).to(dt).cuda()
     yd = torch.empty_like(xd)
-    ctx.apply(g, vd, xd, yd, shift_beta=beta)
+    ctx.apply(g, vd, xd, yd, shift_beta=beta, direct=direct)
     torch.cuda.synchronize()
     xr = xd.cpu().numpy().astype(np.complex128)     # the values the GPU saw
     _bound_check(A, xr, yd.cpu().numpy().astype(np.complex128), TOL[prec])
