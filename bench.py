@@ -57,6 +57,8 @@ def _args():
     p.add_argument("--kernel-workload", default="tectonic")
     p.add_argument("--kernel-nrhs", type=int, default=4)
     p.add_argument("--kernel-prec", type=int, default=32, choices=[32, 64])
+    p.add_argument("--kernel-cfg", default="auto",
+                   help="complex64 kernel configuration: auto, tune, all, or an id")
     return p.parse_args()
 
 
@@ -397,28 +399,38 @@ def run_kernel(args):
     x = torch.randn((R,) + wl.shape, dtype=dt, device="cuda")
     y = torch.empty_like(x)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
-        ctx.apply(g, vd, x, y)
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        ctx.apply(g, vd, x, y)
-        e1.record()
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
-    ms = statistics.median(ts)
-    cb = 8 if args.kernel_prec == 32 else 16
-    algo = 2 * cb * wl.n_points * R + 4 * wl.n_points
-    peaks = _peaks()
-    peak = peaks["hbm_gbs"] if peaks else 6800.0
-    print(json.dumps({"kernel": f"hx_apply_operator fp{args.kernel_prec}", "workload": wl.name,
-                      "nrhs": R, "points": wl.n_points, "ms": round(ms, 4),
-                      "Gpoint_rhs_per_s": round(wl.n_points * R / ms / 1e6, 3),
-                      "algo_bytes": algo, "achieved_gbs": round(algo / ms / 1e6, 1),
-                      "peak_gbs": peak, "frac": round(algo / ms / 1e6 / peak, 4)}), flush=True)
+    if args.kernel_cfg == "tune":
+        best, tms = ctx.autotune(g, vd, R)
+        cfgs = [-1]
+    elif args.kernel_cfg == "all":
+        cfgs = list(range(len(B.kernel_configs())))
+    else:
+        cfgs = [-1 if args.kernel_cfg == "auto" else int(args.kernel_cfg)]
+    for cfg in cfgs:
+        ctx.set_kernel_config(cfg)
+        for _ in range(args.warmup):
+            ctx.apply(g, vd, x, y)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.apply(g, vd, x, y)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        ms = statistics.median(ts)
+        cb = 8 if args.kernel_prec == 32 else 16
+        algo = 2 * cb * wl.n_points * R + 4 * wl.n_points
+        peaks = _peaks()
+        peak = peaks["hbm_gbs"] if peaks else 6800.0
+        print(json.dumps({"kernel": f"hx_apply_operator fp{args.kernel_prec}", "workload": wl.name,
+                          "nrhs": R, "cfg": cfg if cfg >= 0 else args.kernel_cfg,
+                          "points": wl.n_points, "ms": round(ms, 4),
+                          "Gpoint_rhs_per_s": round(wl.n_points * R / ms / 1e6, 3),
+                          "algo_bytes": algo, "achieved_gbs": round(algo / ms / 1e6, 1),
+                          "peak_gbs": peak, "frac": round(algo / ms / 1e6 / peak, 4)}), flush=True)
 
 
 def main():

@@ -139,6 +139,22 @@ int hx_apply_operator(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
                       double shift_beta, const void* x_dev, void* y_dev,
                       int nrhs, int precision, void* stream);
 
+/* Kinds of hx_stencil_sweep. */
+enum { HX_SWEEP_RESIDUAL = 1, HX_SWEEP_JACOBI = 2 };
+
+/* The two stencil sweeps of the multigrid preconditioner, exposed for
+ * callers that build their own smoothers (not in the paper, whose solver is
+ * direct).  A_beta is the operator of hx_apply_operator with shift_beta.
+ *   HX_SWEEP_RESIDUAL: y = b - A_beta x   (b_dev NULL: y = -A_beta x);
+ *   HX_SWEEP_JACOBI:   y = x + omega D^-1 (b - A_beta x), D the diagonal of
+ *                      A_beta (b_dev required).
+ * precision 32 (complex64, FP32) or 64 (complex128, FP64); x_dev, b_dev,
+ * y_dev are [nrhs][nz][ny][nx]; y must overlap neither x nor b.
+ * Asynchronous on stream.  Errors: HX_ERR_ARG, HX_ERR_STATE, HX_ERR_CUDA. */
+int hx_stencil_sweep(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, double shift_beta,
+                     int kind, const void* x_dev, const void* b_dev, void* y_dev, int nrhs,
+                     int precision, double omega, void* stream);
+
 /* The 27 complex128 coefficients of every row of A (same definition as
  * hx_apply_operator, FP64), written to coef_dev as [N][27][2] doubles in
  * offset order (dk, dj, di) with each of dk, dj, di running -1, 0, 1
@@ -180,6 +196,38 @@ int hx_assemble_csr(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
 int hx_assemble_csr_noalloc(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
                             double shift_beta, int64_t* rowptr, int32_t* col,
                             double* val, int64_t nnz_cap, int64_t* nnz_out, void* stream);
+
+/* ---------------------------------------------------------------- tuning */
+
+/* The complex64 operator kernel (used by hx_apply_operator with precision 32
+ * and by every complex64 stencil sweep of hx_solve on grids above the
+ * direct-kernel size) exists in several launch configurations: tile rows per
+ * thread x right-hand sides per CTA.  All compute the same operator (results
+ * differ only in FP32 rounding order); their speed depends on the grid and
+ * nrhs.  The paper has no counterpart (its solver is a sparse direct
+ * factorisation); this only chooses between launch shapes.
+ * hx_kernel_config_info returns the number of configurations and, for a
+ * valid cfg, writes its rows per thread and RHS per CTA (either pointer may
+ * be NULL).  Needs no context. */
+int hx_kernel_config_info(int cfg, int* rows_per_thread, int* rhs_per_cta);
+
+/* Force configuration cfg for every later complex64 launch on ctx; cfg = -1
+ * restores the automatic choice (the hx_autotune result recorded for the
+ * launch's grid size and nrhs, else a default by nrhs).  Errors: HX_ERR_ARG. */
+int hx_set_kernel_config(hx_ctx* ctx, int cfg);
+
+/* Time every configuration of the complex64 apply (shifted form, nrhs
+ * fields, one warm-up then ncalls launches each, CUDA events on stream) on
+ * this grid and velocity, and record the fastest for (nx, ny, nz, nrhs) in
+ * ctx; later hx_apply_operator / hx_solve launches of that size use it.
+ *   best_cfg: receives the chosen configuration (may be NULL);
+ *   ms_out:   receives up to ms_cap per-launch times in ms, by configuration
+ *             (may be NULL).
+ * Allocates two temporary complex64 fields (nrhs * N each) and frees them;
+ * synchronises stream; refuses to run while stream is being captured
+ * (HX_ERR_STATE).  Errors: HX_ERR_ARG, HX_ERR_STATE, HX_ERR_OOM, HX_ERR_CUDA. */
+int hx_autotune(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, int nrhs, int ncalls,
+                int* best_cfg, double* ms_out, int ms_cap, void* stream);
 
 /* ---------------------------------------------------------------- solve */
 

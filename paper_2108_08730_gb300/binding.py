@@ -23,7 +23,8 @@ STATUS = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_OOM", -3: "HX_ERR_NOT_CONVER
 EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_error",
            "hx_set_table", "hx_apply_operator", "hx_row_coefficients", "hx_assemble_csr",
            "hx_solve_default_opts", "hx_solve", "hx_profile", "hx_profile_read",
-           "hx_assemble_csr_noalloc")
+           "hx_assemble_csr_noalloc", "hx_kernel_config_info", "hx_set_kernel_config",
+           "hx_autotune", "hx_stencil_sweep")
 
 NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
 APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
@@ -31,6 +32,7 @@ APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
 PROF_KINDS = {"apply32": 0, "smooth32": 1, "apply64": 2, "smooth64": 3}
 
 SOLVE_MIXED, SOLVE_FP64 = 0, 1
+SWEEP_RESIDUAL, SWEEP_JACOBI = 1, 2
 
 
 class HxError(RuntimeError):
@@ -97,6 +99,10 @@ def lib():
     L.hx_solve.argtypes = [vp, C.POINTER(hx_grid), vp, C.POINTER(hx_source), i, i, vp,
                            C.POINTER(hx_solve_opts), C.POINTER(hx_solve_report), vp]
     L.hx_assemble_csr_noalloc.argtypes = L.hx_assemble_csr.argtypes
+    L.hx_stencil_sweep.argtypes = [vp, C.POINTER(hx_grid), vp, d, i, vp, vp, vp, i, i, d, vp]
+    L.hx_kernel_config_info.argtypes = [i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.hx_set_kernel_config.argtypes = [vp, i]
+    L.hx_autotune.argtypes = [vp, C.POINTER(hx_grid), vp, i, i, C.POINTER(C.c_int), dp, i, vp]
     L.hx_profile.argtypes = [vp, i]
     L.hx_profile_read.argtypes = [vp, i, C.POINTER(C.c_int64), dp, dp]
     for name in EXPORTS:
@@ -126,6 +132,18 @@ def build_weight_table(theta_deg=(0, 10, 20, 30, 40, 45), phi_deg=(0, 10, 20, 30
         raise HxError(st, "hx_build_weight_table failed")
     T = out[:7 * n_g.value].reshape(n_g.value, 7)
     return np.arange(n_g.value) * d_inv_g, T
+
+
+def kernel_configs():
+    """[(rows per thread, RHS per CTA)] of the complex64 kernel configurations."""
+    L = lib()
+    n = L.hx_kernel_config_info(-1, None, None)
+    out = []
+    for c in range(n):
+        a, b = C.c_int(0), C.c_int(0)
+        L.hx_kernel_config_info(c, C.byref(a), C.byref(b))
+        out.append((a.value, b.value))
+    return out
 
 
 def default_opts(**kw):
@@ -217,6 +235,19 @@ class Context:
                                             C.c_void_p(y.data_ptr()), nrhs, prec, _stream_ptr(stream)),
                     "hx_apply_operator")
 
+    def sweep(self, grid, v, kind, x, b, y, shift_beta=0.0, omega=0.6, stream=None):
+        """hx_stencil_sweep: kind 'residual' (y = b - A x; b may be None) or
+        'jacobi' (y = x + omega D^-1 (b - A x))."""
+        import torch
+        prec = 32 if x.dtype == torch.complex64 else 64
+        nrhs = x.shape[0] if x.dim() == 4 else 1
+        k = {"residual": SWEEP_RESIDUAL, "jacobi": SWEEP_JACOBI}[kind]
+        bp = C.c_void_p(b.data_ptr()) if b is not None else C.c_void_p(0)
+        self._check(lib().hx_stencil_sweep(self._h, C.byref(grid), C.c_void_p(v.data_ptr()),
+                                           float(shift_beta), k, C.c_void_p(x.data_ptr()), bp,
+                                           C.c_void_p(y.data_ptr()), nrhs, prec, float(omega),
+                                           _stream_ptr(stream)), "hx_stencil_sweep")
+
     def row_coefficients(self, grid, v, coef, shift_beta=0.0, stream=None):
         self._check(lib().hx_row_coefficients(self._h, C.byref(grid), C.c_void_p(v.data_ptr()),
                                               float(shift_beta), C.c_void_p(coef.data_ptr()),
@@ -239,6 +270,20 @@ class Context:
         if check:
             self._check(st, "hx_solve")
         return rep.as_dict()
+
+    def set_kernel_config(self, cfg):
+        """Force a complex64 kernel configuration (-1: automatic)."""
+        self._check(lib().hx_set_kernel_config(self._h, int(cfg)), "hx_set_kernel_config")
+
+    def autotune(self, grid, v, nrhs, ncalls=3, stream=None):
+        """hx_autotune -> (best configuration, [ms per launch by configuration])."""
+        n = lib().hx_kernel_config_info(-1, None, None)
+        best = C.c_int(-1)
+        ms = (C.c_double * n)()
+        self._check(lib().hx_autotune(self._h, C.byref(grid), C.c_void_p(v.data_ptr()), int(nrhs),
+                                      int(ncalls), C.byref(best), ms, n, _stream_ptr(stream)),
+                    "hx_autotune")
+        return best.value, list(ms)
 
     def profile(self, enable=True):
         self._check(lib().hx_profile(self._h, 1 if enable else 0), "hx_profile")

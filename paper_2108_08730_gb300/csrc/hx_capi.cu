@@ -153,6 +153,7 @@ OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double b
     d.plain_lo[a] = lv.lo[a];
     d.plain_hi[a] = lv.hi[a];
   }
+  d.cfg32 = ctx->st32_cfg;   // call sites that know nrhs refine this (ctx_cfg32)
   return d;
 }
 
@@ -319,7 +320,8 @@ int hx_apply_operator(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doub
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if (precision == 32) {
-    const OpDesc<float> d = make_desc<float>(ctx, *lv, v_dev, shift_beta);
+    OpDesc<float> d = make_desc<float>(ctx, *lv, v_dev, shift_beta);
+    d.cfg32 = ctx_cfg32(ctx, grid->nx, grid->ny, grid->nz, nrhs);
     e = direct ? launch_direct_stencil<float>(d, kApply, x_dev, nullptr, y_dev, nrhs, 0.0, s)
                : launch_stencil(d, kApply, x_dev, nullptr, y_dev, nrhs, N, 0.0, s);
   } else {
@@ -328,6 +330,39 @@ int hx_apply_operator(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doub
                : launch_stencil(d, kApply, x_dev, nullptr, y_dev, nrhs, N, 0.0, s);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "apply launch");
+  return HX_OK;
+}
+
+int hx_stencil_sweep(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, double shift_beta,
+                     int kind, const void* x_dev, const void* b_dev, void* y_dev, int nrhs,
+                     int precision, double omega, void* stream) {
+  if (!ctx) return HX_ERR_ARG;
+  int st = check_grid(ctx, grid);
+  if (st) return st;
+  if (!ctx->tab64) return fail(ctx, HX_ERR_STATE, "no weight table set (hx_set_table)");
+  if (kind != HX_SWEEP_RESIDUAL && kind != HX_SWEEP_JACOBI) return fail(ctx, HX_ERR_ARG, "unknown sweep kind");
+  if (!v_dev || !x_dev || !y_dev || nrhs < 1 || (kind == HX_SWEEP_JACOBI && !b_dev))
+    return fail(ctx, HX_ERR_ARG, "null buffer or nrhs < 1");
+  if (x_dev == y_dev || b_dev == y_dev) return fail(ctx, HX_ERR_ARG, "y must overlap neither x nor b");
+  if (precision != 32 && precision != 64) return fail(ctx, HX_ERR_ARG, "precision must be 32 or 64");
+  if (!std::isfinite(shift_beta) || !std::isfinite(omega)) return fail(ctx, HX_ERR_ARG, "non-finite parameter");
+  cudaSetDevice(ctx->device);
+  Level* lv = nullptr;
+  const int nl[3] = {grid->nx, grid->ny, grid->nz};
+  if ((st = get_level(ctx, grid, nl, grid->h, &lv))) return st;
+  const long long N = (long long)grid->nx * grid->ny * grid->nz;
+  const int mode = kind == HX_SWEEP_RESIDUAL ? kResidual : kJacobi;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (precision == 32) {
+    OpDesc<float> d = make_desc<float>(ctx, *lv, v_dev, shift_beta);
+    d.cfg32 = ctx_cfg32(ctx, grid->nx, grid->ny, grid->nz, nrhs);
+    e = launch_stencil(d, mode, x_dev, b_dev, y_dev, nrhs, N, omega, s);
+  } else {
+    const OpDesc<double> d = make_desc<double>(ctx, *lv, v_dev, shift_beta);
+    e = launch_stencil(d, mode, x_dev, b_dev, y_dev, nrhs, N, omega, s);
+  }
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep launch");
   return HX_OK;
 }
 

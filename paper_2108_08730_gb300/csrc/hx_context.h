@@ -47,6 +47,8 @@ struct hx_ctx {
   std::vector<double> table;    // host copy [n_g][7]
   double* tab64 = nullptr;      // derived [n_g][kTabW]
   float* tab32 = nullptr;
+  int st32_cfg = -1;            // forced complex64 kernel configuration (-1: automatic)
+  std::map<std::string, int> tuned;   // hx_autotune choices by grid size and nrhs
   // cached levels, keyed by their defining parameters
   std::map<std::string, std::unique_ptr<hx::Level>> levels;
   std::list<std::string> lru;
@@ -76,6 +78,11 @@ struct hx_ctx {
 namespace hx {
 
 int fail(hx_ctx* ctx, int code, const std::string& msg);
+inline std::string tune_key(int nx, int ny, int nz, int nrhs) {
+  return std::to_string(nx) + "x" + std::to_string(ny) + "x" + std::to_string(nz) + "r" + std::to_string(nrhs);
+}
+// complex64 kernel configuration for a launch on ctx (forced, tuned, or -1)
+int ctx_cfg32(const hx_ctx* ctx, int nx, int ny, int nz, int nrhs);
 int cuda_fail(hx_ctx* ctx, cudaError_t e, const char* where);
 int check_grid(hx_ctx* ctx, const hx_grid* g);
 // Level for grid g evaluated at spacing h_level with n_level nodes per axis

@@ -36,6 +36,7 @@ struct OpDesc {
   T inv_h2;                // 1 / h^2
   const T* axis[3];        // per axis: [n][4] = (up.re, up.im, dn.re, dn.im)
   int plain_lo[3], plain_hi[3];  // nodes whose up = dn = 1/h^2 exactly
+  int cfg32 = -1;          // complex64 kernel configuration (-1: automatic)
 };
 
 enum StencilMode { kApply = 0, kResidual = 1, kJacobi = 2, kJacobi0 = 3 };
@@ -47,6 +48,17 @@ enum StencilMode { kApply = 0, kResidual = 1, kJacobi = 2, kJacobi0 = 3 };
 template <typename T>
 cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const void* b, void* y,
                            int nrhs, long long rstride, double omega_j, cudaStream_t s);
+
+// Complex64 z-marching kernel (hx_stencil32.cu) for kApply / kResidual /
+// kJacobi; cfg selects rows-per-thread and RHS-per-CTA (st32_num_configs()).
+int st32_num_configs();
+cudaError_t launch_stencil32(const OpDesc<float>& op, int mode, int cfg, const void* x, const void* b,
+                             void* y, int nrhs, long long rstride, double omega_j, cudaStream_t s);
+// Reads and clears the device flag a bounded wait of the complex64 kernel
+// sets when it runs out (1 = some wait gave up since the last call).
+int st32_take_timeout();
+// Automatic choice of the complex64 configuration for nrhs fields.
+int st32_default_config(int nrhs);
 
 cudaError_t launch_row_coefficients(const OpDesc<double>& op, double* coef, cudaStream_t s);
 

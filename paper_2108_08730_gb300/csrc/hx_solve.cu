@@ -177,7 +177,9 @@ class Run {
 
   template <typename T>
   OpDesc<T> desc(int l, double beta) const {
-    return make_desc<T>(ctx, *S->lvl[l], l == 0 ? v_fine : (const float*)S->vlev[l].p, beta);
+    OpDesc<T> d = make_desc<T>(ctx, *S->lvl[l], l == 0 ? v_fine : (const float*)S->vlev[l].p, beta);
+    d.cfg32 = ctx_cfg32(ctx, S->n[l][0], S->n[l][1], S->n[l][2], S->R);
+    return d;
   }
 
   // Stencil launch on level l; fine-level launches are timed by the profiler
@@ -349,7 +351,8 @@ class Run {
     const int R = S->R;
     const long long N = S->N[0];
     const size_t fb = (size_t)R * N * 2 * sizeof(T);
-    const OpDesc<T> A = make_desc<T>(ctx, *S->lvlA, v_fine, 0.0);   // the true operator
+    OpDesc<T> A = make_desc<T>(ctx, *S->lvlA, v_fine, 0.0);   // the true operator
+    A.cfg32 = ctx_cfg32(ctx, S->n[0][0], S->n[0][1], S->n[0][2], R);
     void* r = S->r.p;
     void* rhat = S->rhat.p;
     void* p = S->p.p;
@@ -391,6 +394,7 @@ class Run {
       }
       it += kblk;
       HX_CK(cudaStreamSynchronize(stream));
+      if (st32_take_timeout()) return fail(ctx, HX_ERR_TIMEOUT, "a bounded wait of the stencil kernel ran out");
       if (graphed) collect_graph_prof();
       any = false;
       for (int k = 0; k < R; ++k) {

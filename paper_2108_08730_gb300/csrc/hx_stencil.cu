@@ -539,6 +539,12 @@ cudaError_t launch_m(const OpDesc<T>& op, const void* x, const void* b, void* y,
 template <typename T>
 cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const void* b, void* y,
                            int nrhs, long long rstride, double omega_j, cudaStream_t s) {
+  // the complex64 kernel's bulk row copies need a 16-byte aligned x
+  if (sizeof(T) == 4 && mode != kJacobi0 && ((uintptr_t)x & 15) == 0) {
+    const int cfg = op.cfg32 >= 0 && op.cfg32 < st32_num_configs() ? op.cfg32 : st32_default_config(nrhs);
+    return launch_stencil32(reinterpret_cast<const OpDesc<float>&>(op), mode, cfg, x, b, y, nrhs,
+                            rstride, omega_j, s);
+  }
   switch (mode) {
     case kApply: return launch_m<T, kApply>(op, x, b, y, nrhs, rstride, omega_j, s);
     case kResidual: return launch_m<T, kResidual>(op, x, b, y, nrhs, rstride, omega_j, s);

@@ -1,0 +1,99 @@
+// Autotuner of the complex64 operator kernel: times every configuration
+// (rows per thread x RHS per CTA) of the z-marching kernel on a grid and
+// records the fastest per (grid size, nrhs) in the context; launches on that
+// context then use it.  Not part of the paper's method (its solver is a
+// sparse direct factorisation); it only chooses between launch shapes that
+// compute the same operator.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hx_context.h"
+#include "hx_internal.h"
+
+namespace hx {
+
+int ctx_cfg32(const hx_ctx* ctx, int nx, int ny, int nz, int nrhs) {
+  if (ctx->st32_cfg >= 0) return ctx->st32_cfg;
+  auto it = ctx->tuned.find(tune_key(nx, ny, nz, nrhs));
+  return it == ctx->tuned.end() ? -1 : it->second;
+}
+
+}  // namespace hx
+
+using namespace hx;
+
+namespace {
+// rows per thread and RHS per CTA of each configuration (hx_stencil32.cu)
+const int kCfgRows[] = {2, 1, 2, 1, 1};
+const int kCfgRhs[] = {1, 2, 2, 4, 1};
+}  // namespace
+
+extern "C" int hx_kernel_config_info(int cfg, int* rows_per_thread, int* rhs_per_cta) {
+  const int n = st32_num_configs();
+  if (cfg >= 0 && cfg < n) {
+    if (rows_per_thread) *rows_per_thread = kCfgRows[cfg];
+    if (rhs_per_cta) *rhs_per_cta = kCfgRhs[cfg];
+  }
+  return n;
+}
+
+extern "C" int hx_set_kernel_config(hx_ctx* ctx, int cfg) {
+  if (!ctx) return HX_ERR_ARG;
+  if (cfg < -1 || cfg >= st32_num_configs()) return fail(ctx, HX_ERR_ARG, "unknown kernel configuration");
+  ctx->st32_cfg = cfg;
+  return HX_OK;
+}
+
+extern "C" int hx_autotune(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, int nrhs, int ncalls,
+                           int* best_cfg, double* ms_out, int ms_cap, void* stream) {
+  if (!ctx) return HX_ERR_ARG;
+  int st = check_grid(ctx, grid);
+  if (st) return st;
+  if (!ctx->tab64) return fail(ctx, HX_ERR_STATE, "no weight table set (hx_set_table)");
+  if (!v_dev || nrhs < 1 || ncalls < 1) return fail(ctx, HX_ERR_ARG, "need v_dev, nrhs >= 1, ncalls >= 1");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap != cudaStreamCaptureStatusNone)
+    return fail(ctx, HX_ERR_STATE, "hx_autotune cannot run while the stream is being captured");
+  Level* lv = nullptr;
+  const int nl[3] = {grid->nx, grid->ny, grid->nz};
+  if ((st = get_level(ctx, grid, nl, grid->h, &lv))) return st;
+  const long long N = (long long)grid->nx * grid->ny * grid->nz;
+  const size_t fb = (size_t)nrhs * N * 8;
+  void *x = nullptr, *y = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&x, fb);
+  if (e == cudaSuccess) e = cudaMalloc(&y, fb);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, fb, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int n = st32_num_configs();
+  std::vector<double> ms(n, 1e300);
+  OpDesc<float> d = make_desc<float>(ctx, *lv, v_dev, 0.5);   // the shifted form times the full row
+  for (int c = 0; c < n && e == cudaSuccess; ++c) {
+    e = launch_stencil32(d, kApply, c, x, nullptr, y, nrhs, N, 0.0, s);   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int k = 0; k < ncalls && e == cudaSuccess; ++k)
+      e = launch_stencil32(d, kApply, c, x, nullptr, y, nrhs, N, 0.0, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess) ms[c] = t / ncalls;
+  }
+  if (x) cudaFree(x);
+  if (y) cudaFree(y);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+  if (st32_take_timeout()) return fail(ctx, HX_ERR_TIMEOUT, "a bounded wait of the stencil kernel ran out");
+  int best = 0;
+  for (int c = 1; c < n; ++c)
+    if (ms[c] < ms[best]) best = c;
+  ctx->tuned[tune_key(grid->nx, grid->ny, grid->nz, nrhs)] = best;
+  if (best_cfg) *best_cfg = best;
+  for (int c = 0; c < n && c < ms_cap && ms_out; ++c) ms_out[c] = ms[c];
+  return HX_OK;
+}
