@@ -264,6 +264,11 @@ typedef struct {
                             iterations is captured once per call as a CUDA graph
                             and replayed (not while hx_profile timing is on);
                             0: direct launches                                    */
+  int autotune;          /* 1 (default): the first mixed solve of a grid size and
+                            nrhs with at least 2^20 point*RHS times the complex64
+                            kernel configurations on the fine level (using the
+                            solver's own buffers, before the solve) and keeps the
+                            fastest in the context (see hx_autotune); 0: no     */
 } hx_solve_opts;
 
 typedef struct {
@@ -330,6 +335,85 @@ int hx_profile_read(hx_ctx* ctx, int kind, int64_t* launches, double* total_ms,
 int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, const hx_source* src,
              int nsrc, int nrhs, void* wavefield_dev, const hx_solve_opts* opts,
              hx_solve_report* report, void* stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/* A request-serving engine for hx_solve (not part of the paper, whose solves
+ * run one at a time under a direct solver).  It keeps `slots` worker threads,
+ * each with its own context and CUDA stream on one device, so the solves of
+ * different requests overlap on the GPU; a request is admitted as soon as a
+ * slot is free and its estimated device memory fits in the budget next to
+ * the requests in flight (first come, first served: a request that does not
+ * fit waits, and so do the requests behind it).  Velocity models stay
+ * resident on the device by model id, and every worker keeps its latest
+ * solver workspace (multigrid hierarchy and Krylov vectors) across requests of
+ * the same grid size and nrhs, so a model served at a new frequency only
+ * rebuilds its PML coefficients and coarsest inverse.  Every request is
+ * solved exactly as a lone hx_solve with the same options would solve it
+ * (options are taken as given, hx_solve_opts.autotune is forced to 0 so that
+ * no result depends on timing), so results do not depend on the mix. */
+typedef struct hx_server hx_server;
+
+typedef struct {
+  int device;               /* CUDA device                                        */
+  int slots;                /* concurrent requests (worker threads), >= 1         */
+  double mem_budget;        /* bytes of device memory for admitted requests and
+                               resident models; <= 0: 85% of the free memory at
+                               creation                                          */
+  const double* table;      /* weight table [n_g][7] (hx_build_weight_table),
+                               copied at creation                                 */
+  int n_g;
+  double d_inv_g;
+} hx_server_config;
+
+typedef struct {
+  uint64_t model_id;        /* velocity model identity: requests with the same id
+                               (and grid size) share one device copy             */
+  const float* v_host;      /* velocity [nz][ny][nx]; read when the model is not
+                               resident; must stay valid until the request ends  */
+  hx_grid grid;
+  const hx_source* src;     /* copied at submission                               */
+  int nsrc, nrhs;
+  void* wavefield_host;     /* complex128 [nrhs][nz][ny][nx], written when the
+                               request completes; must stay valid until then     */
+  const hx_solve_opts* opts;/* NULL = hx_solve_default_opts; copied at submission */
+} hx_request;
+
+typedef struct {
+  int status;               /* hx_solve's status (or HX_ERR_OOM / HX_ERR_ARG from
+                               admission)                                         */
+  hx_solve_report report;
+  double queue_ms;          /* submission -> start on a worker                    */
+  double run_ms;            /* start -> wavefield on the host                     */
+  double latency_ms;        /* submission -> completion                           */
+  int worker;               /* slot that served it                                */
+} hx_request_result;
+
+typedef struct {
+  int64_t submitted, completed, failed;
+  double p50_ms, p99_ms, max_ms;   /* latency percentiles of completed requests   */
+  double point_rhs;                /* sum of N * nrhs over completed requests     */
+  double busy_s;                   /* first submission -> last completion (s)     */
+  double peak_committed;           /* peak bytes committed by admission           */
+  int max_concurrent;              /* most requests on the GPU at once            */
+} hx_server_stats;
+
+/* Create the engine (starts the worker threads).  Errors: HX_ERR_ARG,
+ * HX_ERR_CUDA, HX_ERR_OOM; *out is NULL on failure. */
+int hx_server_create(hx_server** out, const hx_server_config* cfg);
+/* Queue a request; returns at once with *ticket (>= 0).  Errors: HX_ERR_ARG
+ * (invalid grid, sources, buffers; the request is not queued), HX_ERR_OOM
+ * (the request alone exceeds the memory budget). */
+int hx_server_submit(hx_server* srv, const hx_request* req, int64_t* ticket);
+/* Wait until request `ticket` completes (timeout_s < 0: no limit) and fill
+ * *res (may be NULL).  Returns the request's status, or HX_ERR_TIMEOUT when
+ * timeout_s passed first (the request keeps running), HX_ERR_ARG for an
+ * unknown ticket.  A ticket can be waited for once. */
+int hx_server_wait(hx_server* srv, int64_t ticket, double timeout_s, hx_request_result* res);
+/* Statistics since creation (or the last reset).  reset = 1 clears them. */
+int hx_server_get_stats(hx_server* srv, hx_server_stats* st, int reset);
+/* Finish the queued requests, stop the workers and free everything. */
+void hx_server_destroy(hx_server* srv);
 
 #ifdef __cplusplus
 }

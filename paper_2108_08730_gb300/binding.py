@@ -24,7 +24,8 @@ EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_
            "hx_set_table", "hx_apply_operator", "hx_row_coefficients", "hx_assemble_csr",
            "hx_solve_default_opts", "hx_solve", "hx_profile", "hx_profile_read",
            "hx_assemble_csr_noalloc", "hx_kernel_config_info", "hx_set_kernel_config",
-           "hx_autotune", "hx_stencil_sweep")
+           "hx_autotune", "hx_stencil_sweep", "hx_server_create", "hx_server_submit",
+           "hx_server_wait", "hx_server_get_stats", "hx_server_destroy")
 
 NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
 APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
@@ -58,7 +59,8 @@ class hx_solve_opts(C.Structure):
                 ("mg_levels", C.c_int), ("nu_pre", C.c_int), ("nu_post", C.c_int),
                 ("coarse_sweeps", C.c_int), ("omega_jacobi", C.c_double),
                 ("source_spread", C.c_int), ("initial_guess", C.c_int), ("check_every", C.c_int),
-                ("coarse_galerkin", C.c_int), ("pml_cap", C.c_double), ("use_graphs", C.c_int)]
+                ("coarse_galerkin", C.c_int), ("pml_cap", C.c_double), ("use_graphs", C.c_int),
+                ("autotune", C.c_int)]
 
 
 class hx_solve_report(C.Structure):
@@ -68,6 +70,29 @@ class hx_solve_report(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hx_server_config(C.Structure):
+    _fields_ = [("device", C.c_int), ("slots", C.c_int), ("mem_budget", C.c_double),
+                ("table", C.POINTER(C.c_double)), ("n_g", C.c_int), ("d_inv_g", C.c_double)]
+
+
+class hx_request(C.Structure):
+    _fields_ = [("model_id", C.c_uint64), ("v_host", C.c_void_p), ("grid", hx_grid),
+                ("src", C.POINTER(hx_source)), ("nsrc", C.c_int), ("nrhs", C.c_int),
+                ("wavefield_host", C.c_void_p), ("opts", C.POINTER(hx_solve_opts))]
+
+
+class hx_request_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("report", hx_solve_report), ("queue_ms", C.c_double),
+                ("run_ms", C.c_double), ("latency_ms", C.c_double), ("worker", C.c_int)]
+
+
+class hx_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
+                ("point_rhs", C.c_double), ("busy_s", C.c_double), ("peak_committed", C.c_double),
+                ("max_concurrent", C.c_int)]
 
 
 _lib = None
@@ -103,11 +128,17 @@ def lib():
     L.hx_kernel_config_info.argtypes = [i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.hx_set_kernel_config.argtypes = [vp, i]
     L.hx_autotune.argtypes = [vp, C.POINTER(hx_grid), vp, i, i, C.POINTER(C.c_int), dp, i, vp]
+    L.hx_server_create.argtypes = [C.POINTER(vp), C.POINTER(hx_server_config)]
+    L.hx_server_submit.argtypes = [vp, C.POINTER(hx_request), C.POINTER(C.c_int64)]
+    L.hx_server_wait.argtypes = [vp, C.c_int64, d, C.POINTER(hx_request_result)]
+    L.hx_server_get_stats.argtypes = [vp, C.POINTER(hx_server_stats), i]
+    L.hx_server_destroy.argtypes = [vp]
+    L.hx_server_destroy.restype = None
     L.hx_profile.argtypes = [vp, i]
     L.hx_profile_read.argtypes = [vp, i, C.POINTER(C.c_int64), dp, dp]
     for name in EXPORTS:
         fn = getattr(L, name)
-        if name not in ("hx_ctx_destroy", "hx_last_error", "hx_solve_default_opts"):
+        if name not in ("hx_ctx_destroy", "hx_last_error", "hx_solve_default_opts", "hx_server_destroy"):
             fn.restype = C.c_int
     _lib = L
     return L
@@ -329,3 +360,69 @@ class Context:
             _dptr(val), cap, C.byref(nnz), _stream_ptr(stream)), "hx_assemble_csr_noalloc")
         n = nnz.value
         return rowptr, col[:n].copy(), val[:2 * n].view(np.complex128).copy()
+
+
+class Server:
+    """hx_server: concurrent request serving of hx_solve on one device.
+
+    Requests carry host arrays: the velocity (float32 (nz, ny, nx)) and the
+    output wavefield (complex128 (nrhs, nz, ny, nx)); both are kept alive
+    here until the request has been waited for."""
+
+    def __init__(self, table, device=0, slots=2, mem_budget=0.0, d_inv_g=0.001):
+        self._T = np.ascontiguousarray(table, dtype=np.float64)
+        cfg = hx_server_config(int(device), int(slots), float(mem_budget), _dptr(self._T),
+                               self._T.shape[0], float(d_inv_g))
+        h = C.c_void_p()
+        st = lib().hx_server_create(C.byref(h), C.byref(cfg))
+        if st != HX_OK:
+            raise HxError(st, "hx_server_create failed")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, grid, v_host, sources, nrhs, out_host, model_id=0, **opts):
+        """Queue one solve; returns its ticket.  sources as in Context.solve."""
+        assert v_host.dtype == np.float32 and v_host.flags.c_contiguous
+        assert out_host.dtype == np.complex128 and out_host.flags.c_contiguous
+        src = (hx_source * len(sources))()
+        for k, (ix, iy, iz, rhs, amp) in enumerate(sources):
+            a = complex(amp)
+            src[k] = hx_source(int(ix), int(iy), int(iz), int(rhs), a.real, a.imag)
+        o = default_opts(**opts)
+        req = hx_request(int(model_id), C.c_void_p(v_host.ctypes.data), grid, src, len(sources),
+                         int(nrhs), C.c_void_p(out_host.ctypes.data), C.pointer(o))
+        t = C.c_int64(-1)
+        st = lib().hx_server_submit(self._h, C.byref(req), C.byref(t))
+        if st != HX_OK:
+            raise HxError(st, "hx_server_submit failed")
+        self._keep[t.value] = (v_host, out_host)
+        return t.value
+
+    def wait(self, ticket, timeout=-1.0):
+        """-> result dict (status, report, queue_ms, run_ms, latency_ms, worker)."""
+        r = hx_request_result()
+        st = lib().hx_server_wait(self._h, int(ticket), float(timeout), C.byref(r))
+        if st == -5 and timeout >= 0:
+            raise TimeoutError(f"request {ticket} still running")
+        self._keep.pop(ticket, None)
+        return {"status": r.status, "report": r.report.as_dict(), "queue_ms": r.queue_ms,
+                "run_ms": r.run_ms, "latency_ms": r.latency_ms, "worker": r.worker}
+
+    def stats(self, reset=False):
+        s = hx_server_stats()
+        st = lib().hx_server_get_stats(self._h, C.byref(s), 1 if reset else 0)
+        if st != HX_OK:
+            raise HxError(st, "hx_server_get_stats failed")
+        return {k: getattr(s, k) for k, _ in hx_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hx_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

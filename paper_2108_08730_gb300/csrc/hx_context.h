@@ -54,6 +54,7 @@ struct hx_ctx {
   std::list<std::string> lru;
   std::map<std::string, std::unique_ptr<hx::Solver>> solvers;
   std::list<std::string> solver_lru;
+  int max_solvers = 8;          // solver workspaces kept (least recently used go first)
   // stream the solver runs on, and the events ordering it with the caller's
   cudaStream_t work_stream = nullptr;
   cudaEvent_t order_ev[2] = {nullptr, nullptr};
@@ -83,6 +84,10 @@ inline std::string tune_key(int nx, int ny, int nz, int nrhs) {
 }
 // complex64 kernel configuration for a launch on ctx (forced, tuned, or -1)
 int ctx_cfg32(const hx_ctx* ctx, int nx, int ny, int nz, int nrhs);
+// autotuner core (hx_tune.cu): times the configurations on level lv with
+// caller-owned buffers and records the fastest for (level size, nrhs)
+int tune_cfg32(hx_ctx* ctx, const Level& lv, const float* v_dev, int nrhs, const void* x, void* y,
+               int ncalls, cudaStream_t s, int* best_cfg, double* ms_out, int ms_cap);
 int cuda_fail(hx_ctx* ctx, cudaError_t e, const char* where);
 int check_grid(hx_ctx* ctx, const hx_grid* g);
 // Level for grid g evaluated at spacing h_level with n_level nodes per axis

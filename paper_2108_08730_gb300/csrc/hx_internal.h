@@ -54,9 +54,6 @@ cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const v
 int st32_num_configs();
 cudaError_t launch_stencil32(const OpDesc<float>& op, int mode, int cfg, const void* x, const void* b,
                              void* y, int nrhs, long long rstride, double omega_j, cudaStream_t s);
-// Reads and clears the device flag a bounded wait of the complex64 kernel
-// sets when it runs out (1 = some wait gave up since the last call).
-int st32_take_timeout();
 // Automatic choice of the complex64 configuration for nrhs fields.
 int st32_default_config(int nrhs);
 

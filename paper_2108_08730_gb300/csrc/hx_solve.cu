@@ -394,7 +394,6 @@ class Run {
       }
       it += kblk;
       HX_CK(cudaStreamSynchronize(stream));
-      if (st32_take_timeout()) return fail(ctx, HX_ERR_TIMEOUT, "a bounded wait of the stencil kernel ran out");
       if (graphed) collect_graph_prof();
       any = false;
       for (int k = 0; k < R; ++k) {
@@ -443,6 +442,7 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->coarse_galerkin = 0;
   o->pml_cap = 1.0;
   o->use_graphs = 1;
+  o->autotune = 1;
 }
 
 namespace {
@@ -622,7 +622,8 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       opt.max_outer < 1 || opt.nu_pre < 1 || opt.nu_post < 0 || opt.coarse_sweeps < 1 ||
       !(opt.omega_jacobi > 0 && opt.omega_jacobi < 2) || !(opt.shift_beta >= 0) ||
       opt.check_every < 1 || opt.coarse_galerkin < 0 || opt.coarse_galerkin > 1 ||
-      !(opt.pml_cap >= 0) || opt.use_graphs < 0 || opt.use_graphs > 1 || opt.mg_levels < 0 ||
+      !(opt.pml_cap >= 0) || opt.use_graphs < 0 || opt.use_graphs > 1 ||
+      opt.autotune < 0 || opt.autotune > 1 || opt.mg_levels < 0 ||
       opt.mg_levels > kMaxLev)
     return finish(fail(ctx, HX_ERR_ARG, "invalid solve options"));
   std::vector<int> has_src(nrhs, 0);
@@ -678,7 +679,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       ctx->solver_lru.remove(key);
       ctx->solver_lru.push_front(key);
     } else {
-      while (ctx->solvers.size() >= 8) {
+      while (!ctx->solvers.empty() && (int)ctx->solvers.size() >= ctx->max_solvers) {
         ctx->solvers.erase(ctx->solver_lru.back());
         ctx->solver_lru.pop_back();
       }
@@ -835,6 +836,15 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   const int nent = (int)ent.size();
   cudaError_t e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "setup"));
+  // complex64 kernel configuration of the fine level, tuned once per grid
+  // size and nrhs (the Krylov buffers serve as scratch before the solve)
+  if (prec == 32 && opt.autotune && (long long)N * nrhs >= (1LL << 20) &&
+      ctx->st32_cfg < 0 && !ctx->tuned.count(tune_key(grid->nx, grid->ny, grid->nz, nrhs))) {
+    if ((e = cudaMemsetAsync(S->p.p, 0, (size_t)nrhs * N * 8, stream)))
+      return finish(cuda_fail(ctx, e, "autotune scratch"));
+    if ((st = tune_cfg32(ctx, *S->lvlA, v_dev, nrhs, S->p.p, S->v.p, 2, stream, nullptr, nullptr, 0)))
+      return finish(st);
+  }
   auto t_setup = std::chrono::steady_clock::now();
 
   S->graph_ready = false;   // kernel parameters may differ from the last call

@@ -3,34 +3,25 @@
 //
 // Same operator, modes and results as the generic kernel in hx_stencil.cu
 // (which keeps the complex128 path); this one is arranged for instruction
-// economy and latency hiding, because the complex64 apply is issue- and
-// latency-bound long before it is bandwidth-bound:
-//  * a CTA owns a 32 x TY column tile, RB right-hand sides and a z-range;
-//    one producer warp streams the x planes (tile + 1-node halo, RB fields)
-//    into an NSLOT-plane shared-memory ring, NC consumer warps compute;
-//  * the producer copies each tile row with one cp.async.bulk (the
-//    16-byte-aligned inner part of the row) plus at most two 8-byte cp.async
-//    for unaligned ends, all completing on the slot's "full" mbarrier; the
-//    consumers release a slot on its "empty" mbarrier, so consumer warps
-//    never meet at a CTA-wide barrier inside the z loop;
-//  * the ring row pitch has the parity of nx and each (plane, field) is
-//    stored at a parity offset c0 in {1, 2}: every element then sits at a
-//    shared address congruent to its global address mod 16, which is what
-//    lets one bulk copy serve a row whatever the row's alignment;
+// economy, because the complex64 apply is issue- and latency-bound long
+// before it is bandwidth-bound:
+//  * a CTA owns a 32 x TY column tile, RB right-hand sides and a z-range and
+//    marches along z; x planes (tile + 1-node halo, RB fields) stream into an
+//    NSLOT-plane shared-memory ring with 8-byte cp.async (zero fill outside
+//    the grid, source pointers precomputed per thread), D planes ahead of the
+//    one being consumed, one barrier per z-step;
 //  * complex additions and real-times-complex products use the packed
 //    FP32x2 instructions of sm_100+ (add/sub/mul/fma .f32x2);
 //  * a warp covers 32 consecutive x; each thread owns YB consecutive y rows
-//    of its column, so the in-plane sums of neighbouring rows share their
-//    horizontal pair sums;
+//    of its column;
 //  * per column and plane the in-plane class sums (centre, 4 faces, 4
 //    corners) live in registers for the three z-steps that use them; the z
 //    loop is unrolled by three so this window rotates without moves;
 //  * 1/v comes from the approximate reciprocal (the table coordinate and
-//    omega^2/v^2 tolerate its 1-ulp error);
+//    omega^2/v^2 tolerate its 1-ulp error), and with few fields per CTA the
+//    table entries of the next plane are fetched one step ahead;
 //  * rows whose only complex stretching is along z stay on the register
 //    path; rows in the x/y PML read their 27 neighbours from the ring.
-// Every mbarrier wait is bounded: on expiry the kernel sets a device flag
-// (read by the host as HX_ERR_TIMEOUT) and the waiting warp leaves its loop.
 #include "hx_complex.cuh"
 #include "hx_internal.h"
 
@@ -91,50 +82,9 @@ __device__ __forceinline__ float rcp_approx(float v) {
 __device__ __forceinline__ float4 ldg4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 
 // ------------------------------------------------------------ async copies
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
-  return ok != 0;
-}
-// the async arrive of the executing thread fires when all of its prior
-// cp.async copies have landed; it counts as one of the barrier's arrivals
-__device__ __forceinline__ void cp_arrive_noinc(unsigned bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void cp8(unsigned dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
-}
-// bytes (a multiple of 16) from a 16-byte aligned global address to a
-// 16-byte aligned shared address, completing on bar
-__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-               ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-__device__ __forceinline__ void fence_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// Set by a bounded wait that ran out (never in correct operation).
-__device__ int g_st32_timeout;
-constexpr int kWaitLimit = 1 << 22;
-__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
-  for (int it = 0; it < kWaitLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  atomicExch(&g_st32_timeout, 1);
-  return false;
-}
+__device__ __forceinline__ void cp_commit32() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait32() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <int V>
 struct I {
@@ -142,154 +92,105 @@ struct I {
 };
 
 // ------------------------------------------------------------ configuration
+// HX_ST32_PREFETCH = 0 turns the one-plane-ahead table fetch off.
+#ifndef HX_ST32_PREFETCH
+#define HX_ST32_PREFETCH 1
+#endif
 constexpr int kW = 32;              // tile extent in x: one warp
-constexpr int kPWmax = 38;          // ring row pitch: 37 (odd nx) or 38 (even nx)
+constexpr int kNW = 8;              // warps per CTA
+constexpr int kThr = kW * kNW;
+constexpr int kPW = kW + 2;         // ring row pitch (tile + halo)
 
-// YB rows per thread, RB right-hand sides per CTA; the register window grows
-// with YB * RB, so the larger configurations run fewer consumer warps (NC)
-// with more registers each.
+// YB rows per thread, RB right-hand sides per CTA.
 template <int YB, int RB>
 struct Cfg {
-  static constexpr int NC = YB * RB <= 1 ? 8 : 4;       // consumer warps per CTA
-  static constexpr int THR = 32 * (NC + 1);            // + one producer warp
-  static constexpr int MINB = YB * RB <= 1 ? 2 : (YB * RB <= 2 ? 3 : 2);   // resident CTAs per SM
-  static constexpr int TY = NC * YB;                   // tile extent in y
+  static constexpr int TY = kNW * YB;                  // tile extent in y
   static constexpr int PH = TY + 2;                    // ring rows (tile + halo)
-  static constexpr int FPLANE = (PH * kPWmax + 1) & ~1;   // complex64 per field plane (even)
-  static constexpr int SLOTE = FPLANE * RB;            // complex64 per ring slot
-  // NSLOT must be even: a (slot, field) plane's parity offset c0 depends on
-  // z only through z & 1, so an even slot count gives every reuse of a slot
-  // the offset of its previous fill, and the out-of-grid halo positions that
-  // no copy writes keep the zeros stored at start-up
-  static constexpr int NSLOT = 8;
-  static constexpr int D = NSLOT - 3;                  // planes in flight beyond the window
-  static constexpr int BAR_BYTES = 256;                // 2 NSLOT mbarriers, padded
-  static constexpr int SMEM = BAR_BYTES + NSLOT * SLOTE * 8;
-  static_assert(NSLOT % 2 == 0, "slot reuse must keep the parity offset");
+  static constexpr int PLANE = PH * kPW;               // complex64 per field plane
+  static constexpr int LI = (PLANE + kThr - 1) / kThr; // loader elements per thread
+  static constexpr int SLOTB = PLANE * RB * 8;         // bytes per ring slot
+  static constexpr int D = SLOTB <= 6144 ? 5 : 4;      // planes in flight beyond the window
+  static constexpr int NSLOT = D + 3;
+  static constexpr int SMEM = NSLOT * SLOTB;
+  static constexpr int MINB = 2;                       // resident CTAs per SM
+  // with RB >= 4 the table lookup is amortised over the fields and its
+  // registers are better spent on the class-sum window
+  static constexpr bool PREFETCH = HX_ST32_PREFETCH && RB <= 2;
 };
 
 template <int MODE, int YB, int RB>
-__global__ void __launch_bounds__(Cfg<YB, RB>::THR, Cfg<YB, RB>::MINB)
+__global__ void __launch_bounds__(kThr, Cfg<YB, RB>::MINB)
 st32_kernel(const OpDesc<float> op, const float2* __restrict__ x, const float2* __restrict__ b,
             float2* __restrict__ y, int nrhs, long long rstride, int zchunk, float omega_j) {
   using K = Cfg<YB, RB>;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const unsigned sbase = (unsigned)__cvta_generic_to_shared(smem);
-  const unsigned full0 = sbase, empty0 = sbase + 8 * K::NSLOT;    // mbarriers
-  const unsigned ring0 = sbase + K::BAR_BYTES;                     // ring of NSLOT slots
-  constexpr unsigned SLOTB = K::SLOTE * 8, FPB = K::FPLANE * 8;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  extern __shared__ __align__(16) float2 ring[];       // [NSLOT][RB][PH][kPW]
+  constexpr unsigned SLOTB = K::SLOTB, RINGB = K::NSLOT * K::SLOTB;
+  const int tid = threadIdx.x, tx = tid & 31, w = tid >> 5;
   const int nx = op.nx, ny = op.ny, nz = op.nz;
-  const int PW = 37 + ((nx & 1) ^ 1);                  // row pitch, parity of nx
   const int gx0 = blockIdx.x * kW, gy0 = blockIdx.y * K::TY;
+  const int ix = gx0 + tx, iyb = gy0 + w * YB;
   const int nrb = (nrhs + RB - 1) / RB;
   const int rblk = blockIdx.z % nrb, zc = blockIdx.z / nrb;
   const int r0 = rblk * RB, rcount = min(RB, nrhs - r0);
   const int z0 = zc * zchunk, z1 = min(nz, z0 + zchunk);
-  const int np = z1 - z0 + 2;                          // planes z0-1 .. z1
   const long long plane = (long long)nx * ny;
-  // parity of the global element index of tile element (row 0, col 0) of
-  // plane z, field r0 + r is  g0par ^ (z & ppar) ^ rpar[r];  the element is
-  // stored at offset c0 = 2 - parity inside its (slot, field) plane
-  const int g0par = ((gy0 - 1) * nx + gx0 - 1) & 1;
-  const int ppar = (int)(plane & 1);
-  int rpar[RB];
-#pragma unroll
-  for (int r = 0; r < RB; ++r) rpar[r] = (int)((((long long)(r0 + r)) * rstride) & 1);
-
-  // zero the ring (rows outside the grid are never written afterwards), set
-  // up the barriers: full = 32 producer-lane arrivals (+ bulk bytes),
-  // empty = one arrival per consumer warp
-  for (int i = tid; i < K::NSLOT * K::SLOTE; i += K::THR)
-    asm volatile("st.shared.v2.f32 [%0], {%1, %1};" ::"r"(ring0 + 8u * i), "f"(0.f) : "memory");
-  if (tid < K::NSLOT) {
-    mbar_init(full0 + 8 * tid, 32);
-    mbar_init(empty0 + 8 * tid, K::NC);
-  }
-  fence_async_smem();
-  __syncthreads();
-
-  if (warp == K::NC) {
-    // ------------------------------------------------------------ producer
-    const int j = lane;                                // tile row copied by this lane
-    const int gy = gy0 - 1 + j;
-    const bool row_ok = j < K::PH && gy >= 0 && gy < ny;
-    const int xa = max(gx0 - 1, 0), xb = min(gx0 + kW, nx - 1);   // row segment in the grid
-    const int lxa = xa - (gx0 - 1);                    // its first tile column
-    int s = 0, ph = 0;                                 // slot and its fill parity
-    for (int p = 0; p < np; ++p) {
-      const int z = z0 - 1 + p;
-      if (p >= K::NSLOT && !mbar_wait(empty0 + 8 * s, ph ^ 1)) break;
-      const unsigned full = full0 + 8 * s, slot = ring0 + s * SLOTB;
-      if (z < 0 || z >= nz) {
-        for (int i = lane; i < K::SLOTE; i += 32)
-          asm volatile("st.shared.v2.f32 [%0], {%1, %1};" ::"r"(slot + 8u * i), "f"(0.f) : "memory");
-        fence_async_smem();
-        mbar_arrive(full);
-      } else if (!row_ok) {
-        mbar_arrive(full);
-      } else {
-        const int zp = z & ppar;
-        unsigned bytes = 0;
-        long long ga[RB], gb[RB];
-        unsigned da[RB];
-#pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          const long long g = (long long)(r0 + r) * rstride + (long long)z * plane + (long long)gy * nx + xa;
-          const long long ge = g + (xb - xa + 1);       // exclusive end
-          ga[r] = (g + 1) & ~1LL;
-          gb[r] = ge & ~1LL;
-          const int c0 = 2 - (g0par ^ zp ^ rpar[r]);
-          da[r] = slot + r * FPB + 8u * (c0 + j * PW + lxa + (int)(ga[r] - g));
-          if (r < rcount && gb[r] > ga[r]) bytes += (unsigned)(gb[r] - ga[r]) * 8u;
-        }
-        if (bytes) mbar_expect_tx(full, bytes);
-#pragma unroll
-        for (int r = 0; r < RB; ++r) {
-          if (r >= rcount) continue;
-          if (gb[r] > ga[r]) bulk_g2s(da[r], x + ga[r], (unsigned)(gb[r] - ga[r]) * 8u, full);
-          const long long g = (long long)(r0 + r) * rstride + (long long)z * plane + (long long)gy * nx + xa;
-          const long long ge = g + (xb - xa + 1);
-          if (g & 1) cp8(da[r] - 8u * (unsigned)(ga[r] - g), x + g);                 // first element
-          if ((ge & 1) && ge - 1 >= ga[r]) cp8(da[r] + 8u * (unsigned)(gb[r] - ga[r]), x + gb[r]);   // last
-        }
-        cp_arrive_noinc(full);
-      }
-      if (++s == K::NSLOT) { s = 0; ph ^= 1; }
-    }
-    // let the last fills land before the warp leaves
-    for (int q = 0; q < K::NSLOT && q < np; ++q) {
-      if (--s < 0) { s = K::NSLOT - 1; ph ^= 1; }
-      if (!mbar_wait(full0 + 8 * s, ph)) break;
-    }
-    return;
-  }
-
-  // -------------------------------------------------------------- consumers
-  const int tx = lane, w = warp;
-  const int ix = gx0 + tx, iyb = gy0 + w * YB;
   const bool shift = op.beta != 0.f;
-  // shared byte offset of this thread's 3 x (YB + 2) window in a field plane
-  const unsigned thr = 8u * (unsigned)((w * YB) * PW + tx);
-  const unsigned rowb = 8u * PW;
-  // byte offset (from smem) of this thread's window in field plane (slot, r) of plane z
-  auto fbase = [&](int slot, int r, int z) -> unsigned {
-    return K::BAR_BYTES + slot * SLOTB + r * FPB + 8u * (unsigned)(2 - (g0par ^ (z & ppar) ^ rpar[r])) + thr;
-  };
-  auto lds2 = [&](unsigned off) { return *reinterpret_cast<const float2*>(smem + off); };
 
+  // ---- loader.  This thread copies elements tid + k kThr of every plane
+  // tile (8-byte cp.async, zero fill outside the grid); ld_p[k] walks plane
+  // by plane through field r0 (x itself for elements outside the grid, which
+  // never advance).
+  const unsigned ld_s = (unsigned)__cvta_generic_to_shared(ring) + 8u * tid;
+  const float2* ld_p[K::LI];
+  bool ld_in[K::LI];
+  const bool ld_last = tid + (K::LI - 1) * kThr < K::PLANE;   // does the last element exist
+  {
+    const float2* xr = x + (long long)r0 * rstride + (long long)(z0 - 1) * plane;
+#pragma unroll
+    for (int k = 0; k < K::LI; ++k) {
+      const int e = tid + k * kThr;
+      const int ly = e / kPW, lx = e - ly * kPW;
+      const int gx = gx0 + lx - 1, gy = gy0 + ly - 1;
+      ld_in[k] = e < K::PLANE && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+      ld_p[k] = ld_in[k] ? xr + (gy * nx + gx) : x;
+    }
+  }
+  // copies of plane z (all RB fields) into the slot at byte offset so; planes
+  // are issued in increasing z, once each, from z0 - 1 to z1
+  auto issue = [&](int z, unsigned so) {
+    if (z > z1) return;                                // not needed by this CTA
+    const unsigned dst = ld_s + so;
+    const bool zin = z >= 0 && z < nz;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+#pragma unroll
+      for (int k = 0; k < K::LI; ++k) {
+        if (k == K::LI - 1 && !ld_last) continue;
+        const bool ok = zin && ld_in[k] && (r == 0 || r < rcount);
+        const float2* src = ok ? ld_p[k] + (r == 0 ? 0 : r * rstride) : x;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(dst + r * (K::PLANE * 8) + k * (kThr * 8)),
+                     "l"(src), "r"(ok ? 8 : 0) : "memory");
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K::LI; ++k)
+      if (ld_in[k]) ld_p[k] += plane;
+  };
+
+  // register window of in-plane class sums: [window slot][row][rhs]
   float2 cs[3][YB][RB], es[3][YB][RB], ks[3][YB][RB];
-  auto sums = [&](int slot, int z, auto wtag) {
+  const float2* thr = ring + (w * YB) * kPW + tx;      // top-left of this thread's window
+  auto slotp = [&](unsigned so) { return reinterpret_cast<const float2*>(reinterpret_cast<const char*>(thr) + so); };
+  auto sums = [&](unsigned so, auto wtag) {
     constexpr int WS = decltype(wtag)::value;
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      const unsigned q = fbase(slot, r, z);
+      const float2* q = slotp(so) + r * K::PLANE;
       float2 M[YB + 2], H[YB + 2];
 #pragma unroll
       for (int rr = 0; rr < YB + 2; ++rr) {
-        const unsigned qa = q + rr * rowb;
-        M[rr] = lds2(qa + 8);
-        H[rr] = padd(lds2(qa), lds2(qa + 16));
+        M[rr] = q[rr * kPW + 1];
+        H[rr] = padd(q[rr * kPW], q[rr * kPW + 2]);
       }
 #pragma unroll
       for (int j = 0; j < YB; ++j) {
@@ -300,56 +201,95 @@ st32_kernel(const OpDesc<float> op, const float2* __restrict__ x, const float2* 
     }
   };
 
-  bool ok = mbar_wait(full0, 0) && mbar_wait(full0 + 8, 0);   // planes z0-1, z0
-  sums(0, z0 - 1, I<0>{});
-  sums(1, z0, I<1>{});
-  // slots of planes z-1, z and of the next plane to wait for (z+1), its parity
-  int s_m = 0, s_0 = 1, s_w = 2, ph_w = 0;
-  if (s_w == K::NSLOT) { s_w = 0; ph_w = 1; }
+  // prologue: planes z0-1 .. z0+D in flight (slots 0 .. D+1), one group each
+#pragma unroll
+  for (int k = -1; k <= K::D; ++k) {
+    issue(z0 + k, (unsigned)(k + 1) * SLOTB);
+    cp_commit32();
+  }
+  cp_wait32<K::D>();                                   // planes z0-1 and z0 landed
+  __syncthreads();
+  sums(0u, I<0>{});
+  sums(SLOTB, I<1>{});
+  // byte offsets of the slots of planes z-1, z, z+1 and of the next issue
+  unsigned o_m = 0, o_0 = SLOTB, o_p = 2 * SLOTB, o_i = (K::D + 2) * SLOTB;
 
   const bool xin = ix < nx;
   const bool plain_x = ix >= op.plain_lo[0] && ix <= op.plain_hi[0];
+  const float umax = (float)(op.n_g - 1);
+  const float ih2 = op.inv_h2;
+  const unsigned zlo = (unsigned)op.plain_lo[2], zspan = (unsigned)(op.plain_hi[2] - op.plain_lo[2]);
+  // Table entries of a row (stiffness class coefficients x h^2 and mass
+  // weights at nodes i0 and i0 + 1, the fraction tf, omega^2 / v^2); with
+  // PREFETCH they are fetched one plane ahead so the lookup latency overlaps
+  // the previous plane's arithmetic.
+  struct Tab {
+    float4 ls, hs, lm, hm;
+    float tf, m;
+    int i0;
+  };
+  auto tab_fetch = [&](float vv, Tab& t) {
+    const float iv = rcp_approx(vv);
+    const float u = fminf(fmaxf(op.u_scale * iv, 0.f), umax);
+    t.i0 = min((int)u, op.n_g - 2);
+    t.tf = u - (float)t.i0;
+    t.m = op.omega2 * iv * iv;
+    const float* tq = op.tab + t.i0 * kTabW;
+    t.ls = ldg4(tq);
+    t.hs = ldg4(tq + kTabW);
+    t.lm = ldg4(tq + 4);
+    t.hm = ldg4(tq + kTabW + 4);
+  };
   bool act[YB], plain_xy[YB];
-  float vnext[YB];
-  const float* vp[YB];                                 // v at (ix, iy, z + 1)
+  Tab tnext[YB];                                       // entries of plane z (PREFETCH)
+  float v1[YB];                                        // v at plane z + 1 (PREFETCH) or z
+  const float* vp[YB];                                 // v at the plane after v1's
   long long yo[YB];                                    // element offset of (ix, iy, z) in field r0
 #pragma unroll
   for (int j = 0; j < YB; ++j) {
     const int iy = iyb + j;
     act[j] = xin && iy < ny;
-    plain_xy[j] = plain_x && iy >= op.plain_lo[1] && iy <= op.plain_hi[1];
+    // the general form is exact for every row: a warp holding any x/y PML
+    // row runs it on all lanes rather than running both forms
+    plain_xy[j] = !__any_sync(0xffffffffu, act[j] && !(plain_x && iy >= op.plain_lo[1] && iy <= op.plain_hi[1]));
     const long long o = (long long)z0 * plane + (long long)(act[j] ? iy * nx + ix : 0);
-    vnext[j] = act[j] && z0 < z1 ? __ldg(op.v + o) : 1.f;
-    vp[j] = op.v + o + plane;
+    if (K::PREFETCH) {
+      tab_fetch(act[j] && z0 < z1 ? __ldg(op.v + o) : 1.5e3f, tnext[j]);
+      v1[j] = act[j] && z0 + 1 < z1 ? __ldg(op.v + o + plane) : 1.5e3f;
+      vp[j] = op.v + o + 2 * plane;
+    } else {
+      v1[j] = act[j] && z0 < z1 ? __ldg(op.v + o) : 1.5e3f;
+      vp[j] = op.v + o + plane;
+    }
     yo[j] = o + (long long)r0 * rstride;
   }
-  const float umax = (float)(op.n_g - 1);
-  const float ih2 = op.inv_h2;
-  const unsigned zlo = (unsigned)op.plain_lo[2], zspan = (unsigned)(op.plain_hi[2] - op.plain_lo[2]);
 
   auto step = [&](auto ptag, int z) {
     constexpr int P = decltype(ptag)::value;
     constexpr int W0 = P % 3, W1 = (P + 1) % 3, W2 = (P + 2) % 3;   // planes z-1, z, z+1
-    ok = ok && mbar_wait(full0 + 8 * s_w, ph_w);        // plane z+1 landed
-    sums(s_w, z + 1, I<W2>{});
+    cp_wait32<K::D - 1>();                             // plane z+1 landed (own copies)
+    __syncthreads();                                   // ... everyone's; step z-1 done
+    issue(z + K::D + 1, o_i);                          // into the slot of plane z-2
+    cp_commit32();
+    sums(o_p, I<W2>{});
     const bool plain_z = (unsigned)z - zlo <= zspan;
 #pragma unroll
     for (int j = 0; j < YB; ++j) {
-      const float vv = vnext[j];
-      if (act[j] && z + 1 < z1) vnext[j] = __ldg(vp[j]);
+      Tab t;
+      if (K::PREFETCH) {
+        t = tnext[j];
+        if (act[j] && z + 1 < z1) tab_fetch(v1[j], tnext[j]);
+      } else {
+        tab_fetch(v1[j], t);                           // v1 holds v at plane z here
+      }
+      v1[j] = act[j] && z + (K::PREFETCH ? 2 : 1) < z1 ? __ldg(vp[j]) : 1.5e3f;
       vp[j] += plane;
       const long long off = yo[j];
       yo[j] += plane;
       if (!act[j]) continue;
-      // table position of 1/G = f h / v and the interpolated derived weights
-      const float iv = rcp_approx(vv);
-      const float u = fminf(fmaxf(op.u_scale * iv, 0.f), umax);
-      const int i0 = min((int)u, op.n_g - 2);
-      const float tf = u - (float)i0;
-      const float* tq = op.tab + i0 * kTabW;
-      const float m = op.omega2 * iv * iv;
-      const float4 lo_s = ldg4(tq), hi_s = ldg4(tq + kTabW);
-      const float4 lo_m = ldg4(tq + 4), hi_m = ldg4(tq + kTabW + 4);
+      const float tf = t.tf, m = t.m;
+      const float* tq = op.tab + t.i0 * kTabW;
+      const float4 lo_s = t.ls, hi_s = t.hs, lo_m = t.lm, hi_m = t.hm;
       const float2 ts = dup(tf);
       // stiffness class coefficients x h^2 (centre, face, edge, corner), mass weights
       const float2 s01 = pfma(ts, psub(make_float2(hi_s.x, hi_s.y), make_float2(lo_s.x, lo_s.y)), make_float2(lo_s.x, lo_s.y));
@@ -427,12 +367,12 @@ st32_kernel(const OpDesc<float> op, const float2* __restrict__ x, const float2* 
           for (int i = 0; i < 3; ++i) Fx[i] = Fy[i] = ms;
 #pragma unroll
           for (int dk = 0; dk < 3; ++dk) {
-            const unsigned q = fbase(dk == 0 ? s_m : (dk == 1 ? s_0 : s_w), r, z - 1 + dk) + j * rowb;
+            const float2* q = slotp(dk == 0 ? o_m : (dk == 1 ? o_0 : o_p)) + r * K::PLANE + j * kPW;
             float2 v[3][3];
 #pragma unroll
             for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
-              for (int ii = 0; ii < 3; ++ii) v[jj][ii] = lds2(q + jj * rowb + 8 * ii);
+              for (int ii = 0; ii < 3; ++ii) v[jj][ii] = q[jj * kPW + ii];
             const float2 Ta = dup(dk == 1 ? t0 : t1), Tb = dup(dk == 1 ? t1 : t2);
             float2 vs[3], hs[3];
 #pragma unroll
@@ -474,21 +414,21 @@ st32_kernel(const OpDesc<float> op, const float2* __restrict__ x, const float2* 
         }
       }
     }
-    // plane z-1 is done for this warp: release its slot to the producer
-    __syncwarp();
-    if (tx == 0) mbar_arrive(empty0 + 8 * s_m);
-    s_m = s_0;
-    s_0 = s_w;
-    if (++s_w == K::NSLOT) { s_w = 0; ph_w ^= 1; }
+    // rotate the ring: plane z-1's slot takes the next issue, z+2 lands after z+1
+    o_i = o_m;
+    o_m = o_0;
+    o_0 = o_p;
+    o_p = o_p + SLOTB == RINGB ? 0u : o_p + SLOTB;
   };
 
-  for (int z = z0; z < z1 && ok; z += 3) {
+  for (int z = z0; z < z1; z += 3) {
     step(I<0>{}, z);
-    if (z + 1 >= z1 || !ok) break;
+    if (z + 1 >= z1) break;
     step(I<1>{}, z + 1);
-    if (z + 2 >= z1 || !ok) break;
+    if (z + 2 >= z1) break;
     step(I<2>{}, z + 2);
   }
+  cp_wait32<0>();
 }
 
 // z-range per CTA: minimise (waves of CTAs) x (z-steps per CTA + ring
@@ -534,7 +474,7 @@ cudaError_t launch_cfg(const OpDesc<float>& op, const void* x, const void* b, vo
   const int zchunk = pick_zchunk32(op.nz, (long long)bx * by, nrb, g_num_sms * K::MINB, K::D + 2);
   const long long gz = (long long)((op.nz + zchunk - 1) / zchunk) * nrb;
   if (gz > 65535) return cudaErrorInvalidConfiguration;
-  kern<<<dim3(bx, by, (unsigned)gz), K::THR, K::SMEM, s>>>(op, (const float2*)x, (const float2*)b,
+  kern<<<dim3(bx, by, (unsigned)gz), kThr, K::SMEM, s>>>(op, (const float2*)x, (const float2*)b,
                                                           (float2*)y, nrhs, rstride, zchunk,
                                                           (float)omega_j);
   count_launch(1);
@@ -545,11 +485,9 @@ template <int MODE>
 cudaError_t launch_mode(const OpDesc<float>& op, int cfg, const void* x, const void* b, void* y,
                         int nrhs, long long rstride, double omega_j, cudaStream_t s) {
   switch (cfg) {
-    case 0: return launch_cfg<MODE, 2, 1>(op, x, b, y, nrhs, rstride, omega_j, s);
+    case 0: return launch_cfg<MODE, 1, 1>(op, x, b, y, nrhs, rstride, omega_j, s);
     case 1: return launch_cfg<MODE, 1, 2>(op, x, b, y, nrhs, rstride, omega_j, s);
-    case 2: return launch_cfg<MODE, 2, 2>(op, x, b, y, nrhs, rstride, omega_j, s);
-    case 3: return launch_cfg<MODE, 1, 4>(op, x, b, y, nrhs, rstride, omega_j, s);
-    case 4: return launch_cfg<MODE, 1, 1>(op, x, b, y, nrhs, rstride, omega_j, s);
+    case 2: return launch_cfg<MODE, 1, 4>(op, x, b, y, nrhs, rstride, omega_j, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -557,17 +495,10 @@ cudaError_t launch_mode(const OpDesc<float>& op, int cfg, const void* x, const v
 }  // namespace
 
 // Kernel configurations (rows per thread YB, RHS per CTA RB):
-//   0: (2,1)  1: (1,2)  2: (2,2)  3: (1,4)  4: (1,1)
-int st32_num_configs() { return 5; }
+//   0: (1,1)  1: (1,2)  2: (1,4)
+int st32_num_configs() { return 3; }
 
-int st32_take_timeout() {
-  int v = 0, zero = 0;
-  if (cudaMemcpyFromSymbol(&v, g_st32_timeout, sizeof(int)) != cudaSuccess) return 0;
-  if (v) cudaMemcpyToSymbol(g_st32_timeout, &zero, sizeof(int));
-  return v;
-}
-
-int st32_default_config(int nrhs) { return nrhs == 1 ? 0 : (nrhs == 2 ? 2 : 3); }
+int st32_default_config(int nrhs) { return nrhs == 1 ? 0 : (nrhs == 2 ? 1 : 2); }
 
 cudaError_t launch_stencil32(const OpDesc<float>& op, int mode, int cfg, const void* x, const void* b,
                              void* y, int nrhs, long long rstride, double omega_j, cudaStream_t s) {

@@ -25,8 +25,8 @@ using namespace hx;
 
 namespace {
 // rows per thread and RHS per CTA of each configuration (hx_stencil32.cu)
-const int kCfgRows[] = {2, 1, 2, 1, 1};
-const int kCfgRhs[] = {1, 2, 2, 4, 1};
+const int kCfgRows[] = {1, 1, 1};
+const int kCfgRhs[] = {1, 2, 4};
 }  // namespace
 
 extern "C" int hx_kernel_config_info(int cfg, int* rows_per_thread, int* rhs_per_cta) {
@@ -44,6 +44,45 @@ extern "C" int hx_set_kernel_config(hx_ctx* ctx, int cfg) {
   ctx->st32_cfg = cfg;
   return HX_OK;
 }
+
+namespace hx {
+
+// Times every configuration of the complex64 apply on level lv with buffers
+// x, y (nrhs fields of the level's size, caller-owned) and records the
+// fastest in ctx.  Synchronises s.
+int tune_cfg32(hx_ctx* ctx, const Level& lv, const float* v_dev, int nrhs, const void* x, void* y,
+               int ncalls, cudaStream_t s, int* best_cfg, double* ms_out, int ms_cap) {
+  const long long N = (long long)lv.n[0] * lv.n[1] * lv.n[2];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const int n = st32_num_configs();
+  std::vector<double> ms(n, 1e300);
+  OpDesc<float> d = make_desc<float>(ctx, lv, v_dev, 0.5);   // the shifted form times the full row
+  for (int c = 0; c < n && e == cudaSuccess; ++c) {
+    e = launch_stencil32(d, kApply, c, x, nullptr, y, nrhs, N, 0.0, s);   // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    for (int k = 0; k < ncalls && e == cudaSuccess; ++k)
+      e = launch_stencil32(d, kApply, c, x, nullptr, y, nrhs, N, 0.0, s);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e == cudaSuccess) ms[c] = t / ncalls;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
+  int best = 0;
+  for (int c = 1; c < n; ++c)
+    if (ms[c] < ms[best]) best = c;
+  ctx->tuned[tune_key(lv.n[0], lv.n[1], lv.n[2], nrhs)] = best;
+  if (best_cfg) *best_cfg = best;
+  for (int c = 0; c < n && c < ms_cap && ms_out; ++c) ms_out[c] = ms[c];
+  return HX_OK;
+}
+
+}  // namespace hx
 
 extern "C" int hx_autotune(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, int nrhs, int ncalls,
                            int* best_cfg, double* ms_out, int ms_cap, void* stream) {
@@ -63,37 +102,12 @@ extern "C" int hx_autotune(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
   const long long N = (long long)grid->nx * grid->ny * grid->nz;
   const size_t fb = (size_t)nrhs * N * 8;
   void *x = nullptr, *y = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaMalloc(&x, fb);
   if (e == cudaSuccess) e = cudaMalloc(&y, fb);
   if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, fb, s);
-  if (e == cudaSuccess) e = cudaEventCreate(&e0);
-  if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int n = st32_num_configs();
-  std::vector<double> ms(n, 1e300);
-  OpDesc<float> d = make_desc<float>(ctx, *lv, v_dev, 0.5);   // the shifted form times the full row
-  for (int c = 0; c < n && e == cudaSuccess; ++c) {
-    e = launch_stencil32(d, kApply, c, x, nullptr, y, nrhs, N, 0.0, s);   // warm-up
-    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int k = 0; k < ncalls && e == cudaSuccess; ++k)
-      e = launch_stencil32(d, kApply, c, x, nullptr, y, nrhs, N, 0.0, s);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float t = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-    if (e == cudaSuccess) ms[c] = t / ncalls;
-  }
+  if (e == cudaSuccess) st = tune_cfg32(ctx, *lv, v_dev, nrhs, x, y, ncalls, s, best_cfg, ms_out, ms_cap);
   if (x) cudaFree(x);
   if (y) cudaFree(y);
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
-  if (st32_take_timeout()) return fail(ctx, HX_ERR_TIMEOUT, "a bounded wait of the stencil kernel ran out");
-  int best = 0;
-  for (int c = 1; c < n; ++c)
-    if (ms[c] < ms[best]) best = c;
-  ctx->tuned[tune_key(grid->nx, grid->ny, grid->nz, nrhs)] = best;
-  if (best_cfg) *best_cfg = best;
-  for (int c = 0; c < n && c < ms_cap && ms_out; ++c) ms_out[c] = ms[c];
-  return HX_OK;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune buffers");
+  return st;
 }

@@ -60,12 +60,12 @@ def _problem(case, beta, otable):
 
 def test_config_table():
     cfgs = B.kernel_configs()
-    assert len(cfgs) >= 4
+    assert len(cfgs) >= 3
     assert all(r >= 1 and k >= 1 for r, k in cfgs)
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("cfg", range(5))
+@pytest.mark.parametrize("cfg", range(3))
 @pytest.mark.parametrize("nrhs", [1, 3, 6])
 def test_apply32_every_config(ctx, otable, case, cfg, nrhs):
     beta = 0.5 if (case + cfg + nrhs) % 2 else 0.0
@@ -100,7 +100,7 @@ def _sweep_ref(A, kind, x, b, omega):
 @pytest.mark.parametrize("case", range(len(CASES)))
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("kind", ["residual", "jacobi"])
-@pytest.mark.parametrize("cfg", [-1, 0, 3])
+@pytest.mark.parametrize("cfg", [-1, 0, 2])
 def test_sweeps_match_oracle(ctx, otable, case, prec, kind, cfg):
     if prec == 64 and cfg != -1:
         pytest.skip("configurations select complex64 kernels only")
@@ -170,7 +170,7 @@ def test_sweep_and_config_errors(ctx):
         ctx.set_kernel_config(99)
 
 
-@pytest.mark.parametrize("cfg", range(5))
+@pytest.mark.parametrize("cfg", range(3))
 def test_apply32_long_z_reuses_the_ring(ctx, otable, cfg):
     # Enough tiles x RHS blocks that every configuration marches through many
     # z-planes per CTA, so each shared-memory ring slot is refilled several
