@@ -57,6 +57,15 @@ def _args():
     p.add_argument("--kernel-workload", default="tectonic")
     p.add_argument("--kernel-nrhs", type=int, default=4)
     p.add_argument("--kernel-prec", type=int, default=32, choices=[32, 64])
+    p.add_argument("--serve-requests", type=int, default=12,
+                   help="Poisson-arriving requests of the serving workload (0: skip)")
+    p.add_argument("--serve-slots", type=int, default=4)
+    p.add_argument("--serve-deadline", type=float, default=30.0,
+                   help="per-request solve time limit in s (hx_solve_opts.time_limit_s)")
+    p.add_argument("--serve-only", action="store_true", help="run the serving workload alone")
+    p.add_argument("--kernel-mode", default="apply", choices=["apply", "jacobi", "residual"],
+                   help="apply: y = A x;  jacobi / residual: the preconditioner's sweeps of the "
+                        "shifted operator (beta = 1, omega = 0.6), as inside the solve")
     p.add_argument("--kernel-cfg", default="auto",
                    help="complex64 kernel configuration: auto, tune, all, or an id")
     return p.parse_args()
@@ -191,7 +200,7 @@ def _traffic_per_launch(kind):
         return None
     try:
         rec = json.load(open(path))
-        src = os.path.join(ROOT, "paper_2108_08730_gb300", "csrc", "hx_stencil.cu")
+        src = os.path.join(ROOT, "paper_2108_08730_gb300", "csrc", "hx_stencil32.cu")
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         if rec.get("source_sha") != h:
             return None
@@ -338,8 +347,8 @@ def run_gpu(args):
         tr = _traffic_per_launch(dom)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr,
-                "kernel": {"apply32": "stencil_kernel<float, kApply>",
-                           "smooth32": "stencil_kernel<float, kJacobi|kResidual>",
+                "kernel": {"apply32": "st32_kernel<kApply> (complex64)",
+                           "smooth32": "st32_kernel<kJacobi|kResidual> (complex64)",
                            "apply64": "stencil_kernel<double, ...>",
                            "smooth64": "stencil_kernel<double, kJacobi|kResidual>"}[dom],
                 "launches": n, "algo_bytes_per_launch": by / n,
@@ -351,6 +360,10 @@ def run_gpu(args):
     if world == 1 and not args.no_cpu:
         r, el, reps, desc, cores = oracle_rate()
         cpu = {"value": round(r, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    serving = None
+    if world == 1 and args.serve_requests > 0:
+        serving = run_serving(args, T)
 
     rep = reports[-1]
     line = {
@@ -372,12 +385,79 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "cpu_baseline": cpu,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_serving(args, T, nreq=None, seed0=5000, log=None):
+    """Serving workload (hx_server): seeded requests from synth.serving_request
+    (model family uniform over the four synthetic families, sides
+    log-uniform in 64..256, f ~ U(2, 10) Hz, 1..32 sources, h = 25 m, 8-node
+    PML), Poisson arrivals at a rate giving an offered load of 0.8 x the solo
+    capacity measured on the first requests solved one at a time.  Returns the
+    serving summary (latency percentiles from submission to wavefield on the
+    host, point*RHS/s over the busy interval)."""
+    import numpy as np
+
+    from paper_2108_08730_gb300 import binding as B
+    from paper_2108_08730_gb300 import synth
+
+    nreq = args.serve_requests if nreq is None else nreq
+    reqs = [synth.serving_request(seed0 + k) for k in range(nreq)]
+    work = np.array([r.n_points * r.nrhs for r in reqs], dtype=np.float64)
+    srv = B.Server(T, slots=args.serve_slots)
+
+    def submit(k, wl):
+        out = np.zeros((wl.nrhs,) + wl.shape, dtype=np.complex128)
+        t = srv.submit(B.grid_of(wl), wl.v, B.sources_of(wl), wl.nrhs, out, model_id=seed0 + k,
+                       time_limit_s=args.serve_deadline)
+        return t, out
+
+    # solo capacity: the first requests one at a time (also warms the engine)
+    ncal = min(3, nreq)
+    t0 = time.perf_counter()
+    for k in range(ncal):
+        t, _ = submit(k, reqs[k])
+        r = srv.wait(t)
+        if r["status"] != 0:
+            raise RuntimeError(f"serving calibration request {k} failed: {r}")
+    solo = work[:ncal].sum() / (time.perf_counter() - t0)          # point*RHS/s
+    rate = 0.8 * solo / work.mean()                                   # requests/s
+    srv.stats(reset=True)
+    rng = np.random.default_rng(seed0)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+    tickets = []
+    start = time.perf_counter()
+    for k, wl in enumerate(reqs):
+        dt = arrivals[k] - (time.perf_counter() - start)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(submit(k, wl))
+    res = [srv.wait(t) for t, _ in tickets]
+    st = srv.stats()
+    srv.close()
+    bad = [seed0 + k for k, r in enumerate(res) if r["status"] != 0]
+    iters = [r["report"]["inner_iters"] for r in res]
+    return {"requests": nreq, "slots": args.serve_slots, "completed": st["completed"],
+            "failed": len(bad), "failed_seeds": bad, "deadline_s": args.serve_deadline,
+            "inner_iters_median": float(np.median(iters)), "inner_iters_max": int(max(iters)),
+            "arrival_rate_per_s": round(rate, 4), "offered_load": 0.8,
+            "solo_capacity_mpoint_rhs_s": round(solo / 1e6, 3),
+            "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
+            "latency": "submission to wavefield on the host, completed requests",
+            "max_ms": round(st["max_ms"], 2),
+            "value": round(st["point_rhs"] / st["busy_s"] / 1e6, 4) if st["busy_s"] > 0 else None,
+            "unit": "Mpoint*RHS/s", "max_concurrent": st["max_concurrent"],
+            "peak_committed_gb": round(st["peak_committed"] / 1e9, 2),
+            "mean_point_rhs": float(work.mean()),
+            "recipe": "synth.serving_request seeds 5000.., families uniform over homogeneous / linear "
+                      "gradient / sharp contrast / tectonic, sides log-uniform 64..256, f U(2,10) Hz, "
+                      "1..32 sources, Poisson arrivals"}
 
 
 def run_kernel(args):
@@ -398,7 +478,15 @@ def run_kernel(args):
     dt = torch.complex64 if args.kernel_prec == 32 else torch.complex128
     x = torch.randn((R,) + wl.shape, dtype=dt, device="cuda")
     y = torch.empty_like(x)
+    bb = torch.randn((R,) + wl.shape, dtype=dt, device="cuda") if args.kernel_mode != "apply" else None
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+
+    def launch():
+        if args.kernel_mode == "apply":
+            ctx.apply(g, vd, x, y)
+        else:
+            ctx.sweep(g, vd, args.kernel_mode, x, bb, y, shift_beta=1.0, omega=0.6)
+
     if args.kernel_cfg == "tune":
         best, tms = ctx.autotune(g, vd, R)
         cfgs = [-1]
@@ -409,23 +497,24 @@ def run_kernel(args):
     for cfg in cfgs:
         ctx.set_kernel_config(cfg)
         for _ in range(args.warmup):
-            ctx.apply(g, vd, x, y)
+            launch()
         torch.cuda.synchronize()
         ts = []
         for _ in range(args.steps):
             flush.fill_(1.0)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            ctx.apply(g, vd, x, y)
+            launch()
             e1.record()
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
         ms = statistics.median(ts)
         cb = 8 if args.kernel_prec == 32 else 16
-        algo = 2 * cb * wl.n_points * R + 4 * wl.n_points
+        streams = 2 if args.kernel_mode == "apply" else 3      # x (+ b) read, y written
+        algo = streams * cb * wl.n_points * R + 4 * wl.n_points
         peaks = _peaks()
         peak = peaks["hbm_gbs"] if peaks else 6800.0
-        print(json.dumps({"kernel": f"hx_apply_operator fp{args.kernel_prec}", "workload": wl.name,
+        print(json.dumps({"kernel": f"{args.kernel_mode} fp{args.kernel_prec}", "workload": wl.name,
                           "nrhs": R, "cfg": cfg if cfg >= 0 else args.kernel_cfg,
                           "points": wl.n_points, "ms": round(ms, 4),
                           "Gpoint_rhs_per_s": round(wl.n_points * R / ms / 1e6, 3),
@@ -437,6 +526,10 @@ def main():
     args = _args()
     if args.kernel:
         run_kernel(args)
+    elif args.serve_only:
+        from paper_2108_08730_gb300 import binding as B
+        nodes, T = B.build_weight_table()
+        print(json.dumps({"serving": run_serving(args, T)}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

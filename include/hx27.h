@@ -155,6 +155,34 @@ int hx_stencil_sweep(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doubl
                      int kind, const void* x_dev, const void* b_dev, void* y_dev, int nrhs,
                      int precision, double omega, void* stream);
 
+/* One problem of hx_apply_batched: y = A x on its own grid and velocity. */
+typedef struct {
+  hx_grid grid;
+  const float* v_dev;       /* velocity [nz][ny][nx]                              */
+  const void* x_dev;        /* complex64 [nrhs][nz][ny][nx], 16-byte aligned      */
+  void* y_dev;              /* complex64 [nrhs][nz][ny][nx], not overlapping x    */
+  int nrhs;
+} hx_apply_item;
+
+/* hx_apply_operator (precision 32) for n problems of different sizes in ONE
+ * persistent launch (not in the paper; it batches the subdomains and
+ * requests a server or a domain-decomposed caller holds at once).  The work
+ * is cut into items (problem, 32 x 8 column tile, z-chunk, block of RHS),
+ * largest problems first; resident CTAs take items from a device counter
+ * until none is left, so uneven sizes balance across the SMs.  Every output
+ * equals hx_apply_operator's for the same kernel configuration (the
+ * configuration is the context's forced one, else the default for the
+ * smallest nrhs).  shift_beta as in hx_apply_operator, common to all.
+ * The plan is staged through a pinned host buffer and a device buffer owned
+ * by ctx, sized by the first call (later calls with no more work reuse them;
+ * such calls can be recorded into a CUDA graph: a call made while the stream
+ * is being captured and needing larger buffers fails with HX_ERR_STATE; a
+ * recorded graph reads the plan from the staging buffer when it runs, so
+ * replay it while no other hx_apply_batched call on ctx intervenes).
+ * Asynchronous on stream.  Errors: HX_ERR_ARG, HX_ERR_STATE, HX_ERR_OOM,
+ * HX_ERR_CUDA. */
+int hx_apply_batched(hx_ctx* ctx, const hx_apply_item* items, int n, double shift_beta, void* stream);
+
 /* The 27 complex128 coefficients of every row of A (same definition as
  * hx_apply_operator, FP64), written to coef_dev as [N][27][2] doubles in
  * offset order (dk, dj, di) with each of dk, dj, di running -1, 0, 1
@@ -269,6 +297,10 @@ typedef struct {
                             kernel configurations on the fine level (using the
                             solver's own buffers, before the solve) and keeps the
                             fastest in the context (see hx_autotune); 0: no     */
+  double time_limit_s;   /* > 0: stop at the first convergence check after this
+                            many seconds of solving and return
+                            HX_ERR_NOT_CONVERGED with the best iterate (a
+                            deadline for serving); 0 (default): no limit        */
 } hx_solve_opts;
 
 typedef struct {

@@ -25,7 +25,7 @@ EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_
            "hx_solve_default_opts", "hx_solve", "hx_profile", "hx_profile_read",
            "hx_assemble_csr_noalloc", "hx_kernel_config_info", "hx_set_kernel_config",
            "hx_autotune", "hx_stencil_sweep", "hx_server_create", "hx_server_submit",
-           "hx_server_wait", "hx_server_get_stats", "hx_server_destroy")
+           "hx_server_wait", "hx_server_get_stats", "hx_server_destroy", "hx_apply_batched")
 
 NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
 APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
@@ -60,7 +60,7 @@ class hx_solve_opts(C.Structure):
                 ("coarse_sweeps", C.c_int), ("omega_jacobi", C.c_double),
                 ("source_spread", C.c_int), ("initial_guess", C.c_int), ("check_every", C.c_int),
                 ("coarse_galerkin", C.c_int), ("pml_cap", C.c_double), ("use_graphs", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("time_limit_s", C.c_double)]
 
 
 class hx_solve_report(C.Structure):
@@ -70,6 +70,11 @@ class hx_solve_report(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hx_apply_item(C.Structure):
+    _fields_ = [("grid", hx_grid), ("v_dev", C.c_void_p), ("x_dev", C.c_void_p), ("y_dev", C.c_void_p),
+                ("nrhs", C.c_int)]
 
 
 class hx_server_config(C.Structure):
@@ -128,6 +133,7 @@ def lib():
     L.hx_kernel_config_info.argtypes = [i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.hx_set_kernel_config.argtypes = [vp, i]
     L.hx_autotune.argtypes = [vp, C.POINTER(hx_grid), vp, i, i, C.POINTER(C.c_int), dp, i, vp]
+    L.hx_apply_batched.argtypes = [vp, C.POINTER(hx_apply_item), i, d, vp]
     L.hx_server_create.argtypes = [C.POINTER(vp), C.POINTER(hx_server_config)]
     L.hx_server_submit.argtypes = [vp, C.POINTER(hx_request), C.POINTER(C.c_int64)]
     L.hx_server_wait.argtypes = [vp, C.c_int64, d, C.POINTER(hx_request_result)]
@@ -265,6 +271,16 @@ class Context:
                                             float(shift_beta), C.c_void_p(x.data_ptr()),
                                             C.c_void_p(y.data_ptr()), nrhs, prec, _stream_ptr(stream)),
                     "hx_apply_operator")
+
+    def apply_batched(self, problems, shift_beta=0.0, stream=None):
+        """hx_apply_batched: problems = [(grid, v, x, y)] with complex64 x, y
+        (nrhs, nz, ny, nx) torch CUDA tensors; one persistent launch."""
+        arr = (hx_apply_item * len(problems))()
+        for k, (g, v, x, y) in enumerate(problems):
+            arr[k] = hx_apply_item(g, C.c_void_p(v.data_ptr()), C.c_void_p(x.data_ptr()),
+                                   C.c_void_p(y.data_ptr()), x.shape[0] if x.dim() == 4 else 1)
+        self._check(lib().hx_apply_batched(self._h, arr, len(problems), float(shift_beta),
+                                           _stream_ptr(stream)), "hx_apply_batched")
 
     def sweep(self, grid, v, kind, x, b, y, shift_beta=0.0, omega=0.6, stream=None):
         """hx_stencil_sweep: kind 'residual' (y = b - A x; b may be None) or

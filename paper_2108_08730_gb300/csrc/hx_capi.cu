@@ -210,6 +210,10 @@ void prof_collect(hx_ctx* ctx) {
 }  // namespace hx
 
 hx_ctx::~hx_ctx() {
+  if (grp_ev) cudaEventSynchronize(grp_ev);
+  if (grp_dev) cudaFree(grp_dev);
+  if (grp_host) cudaFreeHost(grp_host);
+  if (grp_ev) cudaEventDestroy(grp_ev);
   for (auto& p : prof_pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -363,6 +367,69 @@ int hx_stencil_sweep(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doubl
     e = launch_stencil(d, mode, x_dev, b_dev, y_dev, nrhs, N, omega, s);
   }
   if (e != cudaSuccess) return cuda_fail(ctx, e, "sweep launch");
+  return HX_OK;
+}
+
+int hx_apply_batched(hx_ctx* ctx, const hx_apply_item* items, int n, double shift_beta, void* stream) {
+  if (!ctx) return HX_ERR_ARG;
+  if (!items || n < 1 || n > (1 << 20)) return fail(ctx, HX_ERR_ARG, "need 1 <= n <= 2^20 items");
+  if (!ctx->tab64) return fail(ctx, HX_ERR_STATE, "no weight table set (hx_set_table)");
+  if (!std::isfinite(shift_beta)) return fail(ctx, HX_ERR_ARG, "shift_beta must be finite");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<GroupProb> probs(n);
+  int min_rhs = 1 << 30;
+  for (int i = 0; i < n; ++i) {
+    const hx_apply_item& it = items[i];
+    int st = check_grid(ctx, &it.grid);
+    if (st) return st;
+    if (!it.v_dev || !it.x_dev || !it.y_dev || it.nrhs < 1) return fail(ctx, HX_ERR_ARG, "null buffer or nrhs < 1");
+    if (it.x_dev == it.y_dev) return fail(ctx, HX_ERR_ARG, "x and y must not overlap");
+    if (((uintptr_t)it.x_dev & 15) != 0) return fail(ctx, HX_ERR_ARG, "x_dev must be 16-byte aligned");
+    Level* lv = nullptr;
+    const int nl[3] = {it.grid.nx, it.grid.ny, it.grid.nz};
+    if ((st = get_level(ctx, &it.grid, nl, it.grid.h, &lv))) return st;
+    probs[i].op = make_desc<float>(ctx, *lv, it.v_dev, shift_beta);
+    probs[i].x = it.x_dev;
+    probs[i].y = it.y_dev;
+    probs[i].nrhs = it.nrhs;
+    probs[i].rstride = (long long)it.grid.nx * it.grid.ny * it.grid.nz;
+    min_rhs = std::min(min_rhs, it.nrhs);
+  }
+  const int cfg = ctx->st32_cfg >= 0 ? ctx->st32_cfg : st32_default_config(min_rhs);
+  std::vector<GroupItem> plan;
+  st32_group_plan(probs.data(), n, cfg, plan);
+  if (plan.size() > (size_t)(1u << 30)) return fail(ctx, HX_ERR_ARG, "too many work items");
+  const size_t pb = ((n * sizeof(GroupProb) + 255) / 256) * 256;
+  const size_t bytes = pb + plan.size() * sizeof(GroupItem) + 256;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cap);
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (ctx->grp_dev_bytes < bytes || ctx->grp_host_bytes < bytes) {
+    if (capturing) return fail(ctx, HX_ERR_STATE, "hx_apply_batched: call once outside stream capture to size its buffers");
+    if (ctx->grp_ev) cudaEventSynchronize(ctx->grp_ev);
+    if (ctx->grp_dev) cudaFree(ctx->grp_dev);
+    if (ctx->grp_host) cudaFreeHost(ctx->grp_host);
+    ctx->grp_dev = ctx->grp_host = nullptr;
+    ctx->grp_dev_bytes = ctx->grp_host_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->grp_dev, 2 * bytes);
+    if (e == cudaSuccess) e = cudaHostAlloc(&ctx->grp_host, 2 * bytes, cudaHostAllocDefault);
+    if (e == cudaSuccess && !ctx->grp_ev) e = cudaEventCreateWithFlags(&ctx->grp_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batched apply buffers");
+    ctx->grp_dev_bytes = ctx->grp_host_bytes = 2 * bytes;
+  } else if (!capturing && ctx->grp_ev) {
+    cudaEventSynchronize(ctx->grp_ev);                // the previous call's upload has been read
+  }
+  unsigned char* h = (unsigned char*)ctx->grp_host;
+  std::memcpy(h, probs.data(), n * sizeof(GroupProb));
+  std::memcpy(h + pb, plan.data(), plan.size() * sizeof(GroupItem));
+  unsigned char* d = (unsigned char*)ctx->grp_dev;
+  int* counter = (int*)(d + bytes - 256);
+  cudaError_t e = cudaMemcpyAsync(d, h, bytes - 256, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !capturing) e = cudaEventRecord(ctx->grp_ev, s);
+  if (e == cudaSuccess)
+    e = launch_stencil32_group(cfg, (const GroupProb*)d, (const GroupItem*)(d + pb), (int)plan.size(), counter, s);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batched apply launch");
   return HX_OK;
 }
 

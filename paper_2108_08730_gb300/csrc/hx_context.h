@@ -72,6 +72,13 @@ struct hx_ctx {
   };
   std::vector<ProfPending> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
+  // hx_apply_batched: device copy of the plan, pinned staging, and the event
+  // after which the staging may be rewritten
+  void* grp_dev = nullptr;
+  size_t grp_dev_bytes = 0;
+  void* grp_host = nullptr;
+  size_t grp_host_bytes = 0;
+  cudaEvent_t grp_ev = nullptr;
 
   ~hx_ctx();
 };

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/hx27.h"
 
@@ -56,6 +57,26 @@ cudaError_t launch_stencil32(const OpDesc<float>& op, int mode, int cfg, const v
                              void* y, int nrhs, long long rstride, double omega_j, cudaStream_t s);
 // Automatic choice of the complex64 configuration for nrhs fields.
 int st32_default_config(int nrhs);
+
+// Grouped complex64 apply (one persistent launch over problems of different
+// sizes): per-problem descriptor and work item of the persistent kernel.
+struct GroupProb {
+  OpDesc<float> op;
+  const void* x;      // complex64 [nrhs][nz][ny][nx]
+  void* y;
+  int nrhs, zchunk;   // zchunk: set by st32_group_plan
+  long long rstride;
+};
+struct GroupItem {
+  int prob, bx, by, bz;   // problem, tile x, tile y, z-chunk * RHS blocks + RHS block
+};
+int st32_config_rhs(int cfg);
+// Chooses each problem's z-chunk and lists the work items (largest problems first).
+void st32_group_plan(GroupProb* probs, int n, int cfg, std::vector<GroupItem>& items);
+// probs_dev / items_dev: device copies of the plan; counter_dev: one int of
+// device scratch (reset here).  Configurations as for launch_stencil32.
+cudaError_t launch_stencil32_group(int cfg, const GroupProb* probs_dev, const GroupItem* items_dev, int nitems,
+                                   int* counter_dev, cudaStream_t s);
 
 cudaError_t launch_row_coefficients(const OpDesc<double>& op, double* coef, cudaStream_t s);
 

@@ -173,7 +173,13 @@ class Run {
  public:
   Run(hx_ctx* c, SolverImpl* s, const hx_grid* g, const float* v0, const hx_solve_opts& o,
       cudaStream_t st)
-      : ctx(c), S(s), grid(g), v_fine(v0), opt(o), stream(st) {}
+      : ctx(c), S(s), grid(g), v_fine(v0), opt(o), stream(st), t0(std::chrono::steady_clock::now()) {}
+
+  // opts.time_limit_s ran out (checked where the host synchronises anyway)
+  bool past_deadline() const {
+    return opt.time_limit_s > 0 &&
+           std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > opt.time_limit_s;
+  }
 
   template <typename T>
   OpDesc<T> desc(int l, double beta) const {
@@ -384,7 +390,7 @@ class Run {
     const int kblk = opt.check_every;
     // graph replay is skipped while the profiler times individual launches
     const bool graphed = opt.use_graphs && !ctx->prof_on && capture_block<T>(A, kblk);
-    while (any && it < max_iter) {
+    while (any && it < max_iter && !past_deadline()) {
       if (graphed) {
         HX_CK(cudaGraphLaunch(S->gexec, stream));
         count_launch(S->graph_kernels);
@@ -415,6 +421,7 @@ class Run {
   const float* v_fine;
   hx_solve_opts opt;
   cudaStream_t stream;
+  std::chrono::steady_clock::time_point t0;
 };
 
 }  // namespace
@@ -443,6 +450,7 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->pml_cap = 1.0;
   o->use_graphs = 1;
   o->autotune = 1;
+  o->time_limit_s = 0.0;
 }
 
 namespace {
@@ -623,7 +631,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       !(opt.omega_jacobi > 0 && opt.omega_jacobi < 2) || !(opt.shift_beta >= 0) ||
       opt.check_every < 1 || opt.coarse_galerkin < 0 || opt.coarse_galerkin > 1 ||
       !(opt.pml_cap >= 0) || opt.use_graphs < 0 || opt.use_graphs > 1 ||
-      opt.autotune < 0 || opt.autotune > 1 || opt.mg_levels < 0 ||
+      opt.autotune < 0 || opt.autotune > 1 || !(opt.time_limit_s >= 0) || opt.mg_levels < 0 ||
       opt.mg_levels > kMaxLev)
     return finish(fail(ctx, HX_ERR_ARG, "invalid solve options"));
   std::vector<int> has_src(nrhs, 0);
@@ -912,7 +920,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
     worst = worst_rel();
     outer = 1;
   } else {
-    while (outer < opt.max_outer && worst > opt.tol) {
+    while (outer < opt.max_outer && worst > opt.tol && !run.past_deadline()) {
       // inner complex64 solve of A d = r / ||r||
       std::vector<double> sc(R);
       std::vector<int> act(R);

@@ -22,6 +22,9 @@
 //    table entries of the next plane are fetched one step ahead;
 //  * rows whose only complex stretching is along z stay on the register
 //    path; rows in the x/y PML read their 27 neighbours from the ring.
+#include <algorithm>
+#include <vector>
+
 #include "hx_complex.cuh"
 #include "hx_internal.h"
 
@@ -118,19 +121,22 @@ struct Cfg {
   static constexpr bool PREFETCH = HX_ST32_PREFETCH && RB <= 2;
 };
 
+// One CTA's work: the 32 x TY column tile (tbx, tby), RHS block and z-chunk
+// packed in tbz (RHS block fastest), of the operator op.  ring: the CTA's
+// dynamic shared memory ([NSLOT][RB][PH][kPW] complex64).
 template <int MODE, int YB, int RB>
-__global__ void __launch_bounds__(kThr, Cfg<YB, RB>::MINB)
-st32_kernel(const OpDesc<float> op, const float2* __restrict__ x, const float2* __restrict__ b,
-            float2* __restrict__ y, int nrhs, long long rstride, int zchunk, float omega_j) {
+__device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2* __restrict__ x,
+                                          const float2* __restrict__ b, float2* __restrict__ y,
+                                          int nrhs, long long rstride, int zchunk, float omega_j,
+                                          int tbx, int tby, int tbz, float2* ring) {
   using K = Cfg<YB, RB>;
-  extern __shared__ __align__(16) float2 ring[];       // [NSLOT][RB][PH][kPW]
   constexpr unsigned SLOTB = K::SLOTB, RINGB = K::NSLOT * K::SLOTB;
   const int tid = threadIdx.x, tx = tid & 31, w = tid >> 5;
   const int nx = op.nx, ny = op.ny, nz = op.nz;
-  const int gx0 = blockIdx.x * kW, gy0 = blockIdx.y * K::TY;
+  const int gx0 = tbx * kW, gy0 = tby * K::TY;
   const int ix = gx0 + tx, iyb = gy0 + w * YB;
   const int nrb = (nrhs + RB - 1) / RB;
-  const int rblk = blockIdx.z % nrb, zc = blockIdx.z / nrb;
+  const int rblk = tbz % nrb, zc = tbz / nrb;
   const int r0 = rblk * RB, rcount = min(RB, nrhs - r0);
   const int z0 = zc * zchunk, z1 = min(nz, z0 + zchunk);
   const long long plane = (long long)nx * ny;
@@ -431,6 +437,42 @@ st32_kernel(const OpDesc<float> op, const float2* __restrict__ x, const float2* 
   cp_wait32<0>();
 }
 
+template <int MODE, int YB, int RB>
+__global__ void __launch_bounds__(kThr, Cfg<YB, RB>::MINB)
+st32_kernel(const OpDesc<float> op, const float2* __restrict__ x, const float2* __restrict__ b,
+            float2* __restrict__ y, int nrhs, long long rstride, int zchunk, float omega_j) {
+  extern __shared__ __align__(16) float2 ring[];       // [NSLOT][RB][PH][kPW]
+  st32_tile<MODE, YB, RB>(op, x, b, y, nrhs, rstride, zchunk, omega_j, blockIdx.x, blockIdx.y, blockIdx.z, ring);
+}
+
+// Persistent form over a list of problems of different sizes: each CTA takes
+// work items (problem, tile x, tile y, RHS block + z-chunk) from a shared
+// counter until the list is exhausted; every item is one st32_tile.
+template <int YB, int RB>
+__global__ void __launch_bounds__(kThr, Cfg<YB, RB>::MINB)
+st32_group_kernel(const GroupProb* __restrict__ probs, const GroupItem* __restrict__ items, int nitems,
+                  int* __restrict__ counter) {
+  extern __shared__ __align__(16) float2 ring[];
+  __shared__ int next;
+  __shared__ GroupProb P;                              // the current item's problem
+  int cur = -1;
+  for (;;) {
+    __syncthreads();                                   // the previous item is done with the ring and P
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int k = next;
+    if (k >= nitems) break;
+    const GroupItem it = items[k];
+    if (it.prob != cur) {
+      if (threadIdx.x == 0) P = probs[it.prob];
+      __syncthreads();
+      cur = it.prob;
+    }
+    st32_tile<kApply, YB, RB>(P.op, (const float2*)P.x, nullptr, (float2*)P.y, P.nrhs, P.rstride, P.zchunk,
+                              0.f, it.bx, it.by, it.bz, ring);
+  }
+}
+
 // z-range per CTA: minimise (waves of CTAs) x (z-steps per CTA + ring
 // prologue), with waves counted against the resident-CTA slots of the SMs.
 int pick_zchunk32(int nz, long long ntiles_xy, int nrb, int slots, int prologue) {
@@ -499,6 +541,80 @@ cudaError_t launch_mode(const OpDesc<float>& op, int cfg, const void* x, const v
 int st32_num_configs() { return 3; }
 
 int st32_default_config(int nrhs) { return nrhs == 1 ? 0 : (nrhs == 2 ? 1 : 2); }
+
+int st32_config_rhs(int cfg) { return cfg == 0 ? 1 : (cfg == 1 ? 2 : 4); }
+
+namespace {
+template <int YB, int RB>
+cudaError_t launch_group_cfg(const GroupProb* probs_dev, const GroupItem* items_dev, int nitems, int* counter,
+                             cudaStream_t s) {
+  using K = Cfg<YB, RB>;
+  auto kern = st32_group_kernel<YB, RB>;
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, K::SMEM);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) attr_set[dev] = true;
+  }
+  if (g_num_sms <= 0) {
+    if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g_num_sms = 152;
+  }
+  const int grid = std::min(nitems, g_num_sms * K::MINB);
+  kern<<<grid, kThr, K::SMEM, s>>>(probs_dev, items_dev, nitems, counter);
+  count_launch(1);
+  return cudaGetLastError();
+}
+}  // namespace
+
+void st32_group_plan(GroupProb* probs, int n, int cfg, std::vector<GroupItem>& items) {
+  if (g_num_sms <= 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g_num_sms = 152;
+  }
+  const int RB = st32_config_rhs(cfg);
+  const int TY = kNW;                                   // every configuration has one row per thread
+  // target z-planes per item: about eight items per resident CTA slot overall
+  double work = 0;
+  for (int i = 0; i < n; ++i) {
+    const GroupProb& P = probs[i];
+    work += (double)((P.op.nx + kW - 1) / kW) * ((P.op.ny + TY - 1) / TY) * ((P.nrhs + RB - 1) / RB) * P.op.nz;
+  }
+  const int zt = std::max(6, (int)(work / (8.0 * 2 * g_num_sms)));
+  items.clear();
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  // largest problems first, so the last items to start are small ones
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)probs[a].op.nx * probs[a].op.ny * probs[a].op.nz * probs[a].nrhs >
+           (double)probs[b].op.nx * probs[b].op.ny * probs[b].op.nz * probs[b].nrhs;
+  });
+  for (int i : order) {
+    GroupProb& P = probs[i];
+    const int nzc = (P.op.nz + zt - 1) / zt;
+    P.zchunk = (P.op.nz + nzc - 1) / nzc;
+    const int bx = (P.op.nx + kW - 1) / kW, by = (P.op.ny + TY - 1) / TY, nrb = (P.nrhs + RB - 1) / RB;
+    for (int zc = 0; zc < nzc; ++zc)
+      for (int y = 0; y < by; ++y)
+        for (int x = 0; x < bx; ++x)
+          for (int r = 0; r < nrb; ++r) items.push_back({i, x, y, zc * nrb + r});
+  }
+}
+
+cudaError_t launch_stencil32_group(int cfg, const GroupProb* probs_dev, const GroupItem* items_dev, int nitems,
+                                   int* counter_dev, cudaStream_t s) {
+  if (nitems <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(counter_dev, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  switch (cfg) {
+    case 0: return launch_group_cfg<1, 1>(probs_dev, items_dev, nitems, counter_dev, s);
+    case 1: return launch_group_cfg<1, 2>(probs_dev, items_dev, nitems, counter_dev, s);
+    case 2: return launch_group_cfg<1, 4>(probs_dev, items_dev, nitems, counter_dev, s);
+  }
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_stencil32(const OpDesc<float>& op, int mode, int cfg, const void* x, const void* b,
                              void* y, int nrhs, long long rstride, double omega_j, cudaStream_t s) {

@@ -200,3 +200,73 @@ def test_apply32_long_z_reuses_the_ring(ctx, otable, cfg):
     bound = (abs(A) @ np.abs(xr).T).T
     assert np.all(np.isfinite(y))
     assert np.max(np.abs(y - ref) / bound) <= TOL[32]
+
+
+def _batch_problems(otable):
+    # uneven sizes, PML on some faces, different nrhs; each with its oracle matrix
+    specs = [((23, 19, 70), (3, 4, 2, 5, 4, 3), 4), ((9, 9, 9), (2,) * 6, 1), ((31, 37, 35), (6, 5, 4, 6, 5, 6), 3),
+             ((40, 64, 161), (5, 6, 4, 5, 6, 5), 2), ((5, 33, 40), (0,) * 6, 5)]
+    out = []
+    nodes, T = otable
+    for k, (shape, npml, nrhs) in enumerate(specs):
+        key = ("batch", k)
+        if key not in _A:
+            v = synth.random_velocity(shape, 400 + k, 1500.0, 4500.0)
+            prof = O.profiles_for(shape, 25.0, npml, 4500.0, 1e-3)
+            _A[key] = (v, O.assemble_csr(v, 25.0, 5.0, prof, T, nodes, beta=0.5),
+                       B.make_grid(shape, 25.0, 5.0, npml, 4500.0))
+        v, A, g = _A[key]
+        x = torch.from_numpy(synth.random_field(shape, nrhs, 90 + k)).to(torch.complex64).cuda()
+        out.append((g, torch.from_numpy(v).cuda(), x, A))
+    return out
+
+
+@pytest.mark.parametrize("cfg", [-1, 0, 1, 2])
+def test_apply_batched_equals_single_applies(ctx, otable, cfg):
+    probs = _batch_problems(otable)
+    ys = [torch.full_like(x, complex(np.nan, np.nan)) for _, _, x, _ in probs]
+    ctx.set_kernel_config(cfg)
+    try:
+        ctx.apply_batched([(g, v, x, y) for (g, v, x, _), y in zip(probs, ys)], shift_beta=0.5)
+        torch.cuda.synchronize()
+        singles = []
+        for g, v, x, _ in probs:
+            y1 = torch.empty_like(x)
+            if cfg >= 0:
+                ctx.apply(g, v, x, y1, shift_beta=0.5)       # same configuration: identical arithmetic
+            singles.append(y1)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_kernel_config(-1)
+    for (g, v, x, A), y, y1 in zip(probs, ys, singles):
+        yy = y.cpu().numpy().astype(np.complex128).reshape(x.shape[0], -1)
+        xr = x.cpu().numpy().astype(np.complex128).reshape(x.shape[0], -1)
+        ref = (A @ xr.T).T
+        bound = (abs(A) @ np.abs(xr).T).T
+        assert np.all(np.isfinite(yy))
+        assert np.max(np.abs(yy - ref) / bound) <= TOL[32]
+        if cfg >= 0:
+            assert torch.equal(y, y1)
+
+
+def test_apply_batched_replays_in_a_cuda_graph(ctx, otable):
+    probs = _batch_problems(otable)
+    ys = [torch.zeros_like(x) for _, _, x, _ in probs]
+    items = [(g, v, x, y) for (g, v, x, _), y in zip(probs, ys)]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ctx.apply_batched(items, shift_beta=0.5, stream=s.cuda_stream)     # sizes the plan buffers
+    torch.cuda.synchronize()
+    want = [y.clone() for y in ys]
+    for y in ys:
+        y.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        ctx.apply_batched(items, shift_beta=0.5, stream=s.cuda_stream)
+    for _ in range(2):
+        for y in ys:
+            y.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        for y, w in zip(ys, want):
+            assert torch.equal(y, w)
