@@ -63,6 +63,10 @@ def _args():
     p.add_argument("--serve-deadline", type=float, default=30.0,
                    help="per-request solve time limit in s (hx_solve_opts.time_limit_s)")
     p.add_argument("--serve-only", action="store_true", help="run the serving workload alone")
+    p.add_argument("--solve-config", default=None, choices=["homogeneous", "linear_gradient",
+                                                             "sharp_contrast", "tectonic"],
+                   help="one mixed solve (and its autotune) of that workload with all its sources")
+    p.add_argument("--solve-time-limit", type=float, default=300.0)
     p.add_argument("--kernel-mode", default="apply", choices=["apply", "jacobi", "residual"],
                    help="apply: y = A x;  jacobi / residual: the preconditioner's sweeps of the "
                         "shifted operator (beta = 1, omega = 0.6), as inside the solve")
@@ -76,6 +80,23 @@ def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def reduce_max_ms(ms, world, device="cpu"):
+    """Slowest rank's time: all-reduce MAX over the process group (identity at N = 1)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, steps, max_total_ms):
+    """Whole-job Mpoint*RHS/s: every rank's units over the slowest rank's time
+    (replicas: each rank solves its own copy of the workload)."""
+    return units_per_rank * world * steps / (max_total_ms / 1e3) / 1e6
 
 
 def _peaks():
@@ -281,14 +302,9 @@ def run_gpu(args):
     prof_step_ms, _ = timed_steps()
     prof = ctx.profile_read()
     ctx.profile(False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max_ms(sum(step_ms), world, dev)
     ms_per_step = total_ms / args.steps
-    value = units * world * args.steps / (total_ms / 1e3) / 1e6
+    value = aggregate_rate(units, world, args.steps, total_ms)
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e_ms = []
@@ -304,13 +320,8 @@ def run_gpu(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = units * world * len(e2e_ms) / (e2e_total / 1e3) / 1e6
+    e2e_total = reduce_max_ms(sum(e2e_ms), world, dev)
+    e2e_value = aggregate_rate(units, world, len(e2e_ms), e2e_total)
 
     if rank != 0:
         if world > 1:
@@ -460,6 +471,41 @@ def run_serving(args, T, nreq=None, seed0=5000, log=None):
                       "1..32 sources, Poisson arrivals"}
 
 
+def run_solve_config(args):
+    """One mixed-precision solve of a full workload (all its sources as RHS):
+    throughput from sources on the device to wavefields on the device, the
+    FP64 relative residual the refinement reached, iteration counts, and the
+    autotuned kernel configuration (tuning done before the timed solve)."""
+    import torch
+
+    from paper_2108_08730_gb300 import binding as B
+    from paper_2108_08730_gb300 import synth
+
+    nodes, T = B.build_weight_table()
+    ctx = B.Context(0, table=T)
+    wl = synth.CONFIGS[args.solve_config]()
+    g = B.grid_of(wl)
+    vd = torch.from_numpy(wl.v).cuda()
+    R = wl.nrhs
+    best, tms = ctx.autotune(g, vd, R)
+    out = torch.zeros((R,) + wl.shape, dtype=torch.complex128, device="cuda")
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    rep = ctx.solve(g, vd, B.sources_of(wl), R, out, check=False, time_limit_s=args.solve_time_limit)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    print(json.dumps({"solve_config": wl.name, "shape": list(wl.shape), "nrhs": R, "points": wl.n_points,
+                      "status": rep["status"], "rel_residual": rep["rel_residual"],
+                      "outer_iters": rep["outer_iters"], "inner_iters": rep["inner_iters"],
+                      "mg_levels": rep["mg_levels"], "ms": round(ms, 1),
+                      "value": round(wl.n_points * R / ms / 1e3, 3), "unit": UNIT,
+                      "kernel_config": best, "config_ms": [round(t, 3) for t in tms],
+                      "G_range": [round(float(wl.v.min()) / (wl.f * wl.h), 2),
+                                  round(float(wl.v.max()) / (wl.f * wl.h), 2)]}), flush=True)
+
+
 def run_kernel(args):
     """Time hx_apply_operator alone (complex64 or complex128) on a full-size
     model: --kernel-workload (tectonic 401x401x187 by default) with
@@ -526,6 +572,8 @@ def main():
     args = _args()
     if args.kernel:
         run_kernel(args)
+    elif args.solve_config:
+        run_solve_config(args)
     elif args.serve_only:
         from paper_2108_08730_gb300 import binding as B
         nodes, T = B.build_weight_table()
