@@ -97,6 +97,18 @@ int hx_build_weight_table(const double* theta_deg, int n_theta,
                           double inv_g_max, double d_inv_g, double lambda,
                           double* table_out, int capacity, int* n_g_out);
 
+/* Non-adaptive weights (Eq. eq_cost of Section 2.2): ONE weight vector fitted
+ * to the plane waves of all n listed 1/G values (and all angle pairs) --
+ * the paper's G4 stencil for {1/4} and Gm for {1/4, 1/6, 1/8, 1/10}.  Minimum-
+ * norm least squares (a single G leaves a 2-dimensional family of minimisers).
+ *   w7_out: caller-owned [7] = [ws1, ws2, ws3, wm1, wm2, wm3, wm4], per-point
+ *           mass weights as in hx_build_weight_table.
+ * A table whose every row is w7 (hx_set_table) makes every operator call
+ * use that fixed stencil.  Needs no context and no GPU.  Errors: HX_ERR_ARG
+ * (1/G outside (0, 0.5], empty lists), HX_ERR_NUMERIC. */
+int hx_fit_joint_weights(const double* inv_g, int n, const double* theta_deg, int n_theta,
+                         const double* phi_deg, int n_phi, double* w7_out);
+
 /* ---------------------------------------------------------------- context */
 
 /* Create a context bound to CUDA device `device`.  *out is NULL on failure. */
@@ -112,6 +124,20 @@ const char* hx_last_error(const hx_ctx* ctx);
  * array may be freed on return.  Synchronous.  Errors: HX_ERR_ARG (n_g < 2,
  * d_inv_g <= 0, non-finite entries), HX_ERR_OOM, HX_ERR_CUDA. */
 int hx_set_table(hx_ctx* ctx, const double* table_host, int n_g, double d_inv_g);
+
+/* Roles of a table in hx_set_table_ex. */
+enum { HX_TABLE_BOTH = 0, HX_TABLE_OPERATOR = 1, HX_TABLE_PRECONDITIONER = 2 };
+
+/* hx_set_table for one role: HX_TABLE_OPERATOR sets the table of the operator
+ * itself (hx_apply_operator, hx_row_coefficients, hx_assemble_csr, the Krylov
+ * operator and FP64 residual of hx_solve) and leaves hx_solve's multigrid
+ * preconditioner on the table it used so far; HX_TABLE_PRECONDITIONER sets the
+ * preconditioner's only (the operator table must exist); HX_TABLE_BOTH is
+ * hx_set_table.  Lets a fixed stencil -- the paper's non-adaptive G4 or Gm
+ * (hx_fit_joint_weights) -- be solved with the adaptive preconditioner,
+ * which only has to approximate A^-1.  Errors as hx_set_table, plus
+ * HX_ERR_STATE. */
+int hx_set_table_ex(hx_ctx* ctx, const double* table_host, int n_g, double d_inv_g, int which);
 
 /* ---------------------------------------------------------------- operator */
 

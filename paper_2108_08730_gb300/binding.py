@@ -25,7 +25,8 @@ EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_
            "hx_solve_default_opts", "hx_solve", "hx_profile", "hx_profile_read",
            "hx_assemble_csr_noalloc", "hx_kernel_config_info", "hx_set_kernel_config",
            "hx_autotune", "hx_stencil_sweep", "hx_server_create", "hx_server_submit",
-           "hx_server_wait", "hx_server_get_stats", "hx_server_destroy", "hx_apply_batched")
+           "hx_server_wait", "hx_server_get_stats", "hx_server_destroy", "hx_apply_batched",
+           "hx_fit_joint_weights", "hx_set_table_ex")
 
 NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
 APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
@@ -114,12 +115,14 @@ def lib():
     L = C.CDLL(LIB_PATH)
     vp, i, d, dp = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double)
     L.hx_build_weight_table.argtypes = [dp, i, dp, i, d, d, d, dp, i, C.POINTER(C.c_int)]
+    L.hx_fit_joint_weights.argtypes = [dp, i, dp, i, dp, i, dp]
     L.hx_ctx_create.argtypes = [C.POINTER(vp), i]
     L.hx_ctx_destroy.argtypes = [vp]
     L.hx_ctx_destroy.restype = None
     L.hx_last_error.argtypes = [vp]
     L.hx_last_error.restype = C.c_char_p
     L.hx_set_table.argtypes = [vp, dp, i, d]
+    L.hx_set_table_ex.argtypes = [vp, dp, i, d, i]
     L.hx_apply_operator.argtypes = [vp, C.POINTER(hx_grid), vp, d, vp, vp, i, i, vp]
     L.hx_row_coefficients.argtypes = [vp, C.POINTER(hx_grid), vp, d, vp, vp]
     L.hx_assemble_csr.argtypes = [vp, C.POINTER(hx_grid), vp, d, C.POINTER(C.c_int64),
@@ -169,6 +172,24 @@ def build_weight_table(theta_deg=(0, 10, 20, 30, 40, 45), phi_deg=(0, 10, 20, 30
         raise HxError(st, "hx_build_weight_table failed")
     T = out[:7 * n_g.value].reshape(n_g.value, 7)
     return np.arange(n_g.value) * d_inv_g, T
+
+
+def fit_joint_weights(inv_g_list, theta_deg=(0, 10, 20, 30, 40, 45), phi_deg=(0, 10, 20, 30, 40, 45)):
+    """hx_fit_joint_weights -> the 7 fixed weights of a non-adaptive stencil
+    (G4: [1/4]; Gm: [1/4, 1/6, 1/8, 1/10])."""
+    ig = np.ascontiguousarray(inv_g_list, dtype=np.float64)
+    th = np.ascontiguousarray(theta_deg, dtype=np.float64)
+    ph = np.ascontiguousarray(phi_deg, dtype=np.float64)
+    w7 = np.zeros(7)
+    st = lib().hx_fit_joint_weights(_dptr(ig), ig.size, _dptr(th), th.size, _dptr(ph), ph.size, _dptr(w7))
+    if st != HX_OK:
+        raise HxError(st, "hx_fit_joint_weights failed")
+    return w7
+
+
+def fixed_table(w7, n_g=401):
+    """A weight table whose every node holds w7 (a non-adaptive stencil)."""
+    return np.tile(np.asarray(w7, dtype=np.float64), (n_g, 1))
 
 
 def kernel_configs():
@@ -254,9 +275,12 @@ class Context:
             msg = lib().hx_last_error(self._h)
             raise HxError(st, f"{what}: {msg.decode() if msg else ''}")
 
-    def set_table(self, table, d_inv_g=0.001):
+    def set_table(self, table, d_inv_g=0.001, role="both"):
+        """hx_set_table_ex with role "both", "operator" or "preconditioner"."""
         T = np.ascontiguousarray(table, dtype=np.float64)
-        self._check(lib().hx_set_table(self._h, _dptr(T), T.shape[0], float(d_inv_g)), "hx_set_table")
+        which = {"both": 0, "operator": 1, "preconditioner": 2}[role]
+        self._check(lib().hx_set_table_ex(self._h, _dptr(T), T.shape[0], float(d_inv_g), which),
+                    "hx_set_table_ex")
 
     def apply(self, grid, v, x, y, shift_beta=0.0, stream=None, direct=False):
         """y = A x; v float32 (nz,ny,nx) and x, y complex64/complex128

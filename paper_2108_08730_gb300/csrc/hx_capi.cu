@@ -136,15 +136,17 @@ int get_level(hx_ctx* ctx, const hx_grid* g, const int nl[3], double hl, Level**
 }
 
 template <typename T>
-OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double beta) {
+OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double beta, bool precond) {
   OpDesc<T> d;
   d.nx = lv.n[0];
   d.ny = lv.n[1];
   d.nz = lv.n[2];
   d.v = v;
-  d.tab = sizeof(T) == 8 ? (const T*)ctx->tab64 : (const T*)ctx->tab32;
-  d.n_g = ctx->n_g;
-  d.u_scale = (T)(lv.f * lv.h / ctx->d_inv_g);
+  const bool pt = precond && ctx->ptab64;
+  if (pt) d.tab = sizeof(T) == 8 ? (const T*)ctx->ptab64 : (const T*)ctx->ptab32;
+  else d.tab = sizeof(T) == 8 ? (const T*)ctx->tab64 : (const T*)ctx->tab32;
+  d.n_g = pt ? ctx->pn_g : ctx->n_g;
+  d.u_scale = (T)(lv.f * lv.h / (pt ? ctx->pd_inv_g : ctx->d_inv_g));
   d.omega2 = (T)((2.0 * M_PI * lv.f) * (2.0 * M_PI * lv.f));
   d.beta = (T)beta;
   d.inv_h2 = (T)(1.0 / (lv.h * lv.h));
@@ -157,8 +159,8 @@ OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double b
   return d;
 }
 
-template OpDesc<float> make_desc<float>(const hx_ctx*, const Level&, const float*, double);
-template OpDesc<double> make_desc<double>(const hx_ctx*, const Level&, const float*, double);
+template OpDesc<float> make_desc<float>(const hx_ctx*, const Level&, const float*, double, bool);
+template OpDesc<double> make_desc<double>(const hx_ctx*, const Level&, const float*, double, bool);
 
 namespace {
 std::atomic<long long> g_launches{0};
@@ -224,6 +226,8 @@ hx_ctx::~hx_ctx() {
   if (work_stream) cudaStreamDestroy(work_stream);
   for (auto e : order_ev)
     if (e) cudaEventDestroy(e);
+  if (ptab64 && ptab64 != tab64) cudaFree(ptab64);
+  if (ptab32 && ptab32 != tab32) cudaFree(ptab32);
   if (tab64) cudaFree(tab64);
   if (tab32) cudaFree(tab32);
 }
@@ -238,6 +242,12 @@ int hx_build_weight_table(const double* theta_deg, int n_theta, const double* ph
   std::string err;
   return build_weight_table(theta_deg, n_theta, phi_deg, n_phi, inv_g_max, d_inv_g, lambda,
                             table_out, capacity, n_g_out, &err);
+}
+
+int hx_fit_joint_weights(const double* inv_g, int n, const double* theta_deg, int n_theta,
+                         const double* phi_deg, int n_phi, double* w7_out) {
+  std::string err;
+  return fit_joint_weights(inv_g, n, theta_deg, n_theta, phi_deg, n_phi, w7_out, &err);
 }
 
 int hx_ctx_create(hx_ctx** out, int device) {
@@ -264,12 +274,9 @@ const char* hx_last_error(const hx_ctx* ctx) {
   return ctx->err.c_str();
 }
 
-int hx_set_table(hx_ctx* ctx, const double* table, int n_g, double d_inv_g) {
-  if (!ctx) return HX_ERR_ARG;
-  if (!table || n_g < 2 || !(d_inv_g > 0)) return fail(ctx, HX_ERR_ARG, "need table, n_g >= 2, d_inv_g > 0");
-  for (int i = 0; i < 7 * n_g; ++i)
-    if (!std::isfinite(table[i])) return fail(ctx, HX_ERR_ARG, "table has non-finite entries");
-  cudaSetDevice(ctx->device);
+namespace {
+// Derived device tables (FP64 and FP32) of a weight table [n_g][7].
+cudaError_t upload_table(const double* table, int n_g, double** t64, float** t32) {
   std::vector<double> d64((size_t)n_g * kTabW, 0.0);
   std::vector<float> d32((size_t)n_g * kTabW, 0.f);
   for (int i = 0; i < n_g; ++i) {
@@ -287,21 +294,72 @@ int hx_set_table(hx_ctx* ctx, const double* table, int n_g, double d_inv_g) {
     o[10] = ws3 / 8.0;
     for (int k = 0; k < kTabW; ++k) d32[(size_t)i * kTabW + k] = (float)o[k];
   }
-  if (ctx->tab64) cudaFree(ctx->tab64);
-  if (ctx->tab32) cudaFree(ctx->tab32);
-  ctx->tab64 = nullptr;
-  ctx->tab32 = nullptr;
-  cudaError_t e = cudaMalloc(&ctx->tab64, d64.size() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&ctx->tab32, d32.size() * sizeof(float));
-  if (e == cudaSuccess) e = cudaMemcpy(ctx->tab64, d64.data(), d64.size() * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(ctx->tab32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  *t64 = nullptr;
+  *t32 = nullptr;
+  cudaError_t e = cudaMalloc(t64, d64.size() * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(t32, d32.size() * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemcpy(*t64, d64.data(), d64.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(*t32, d32.data(), d32.size() * sizeof(float), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    if (*t64) cudaFree(*t64);
+    if (*t32) cudaFree(*t32);
+    *t64 = nullptr;
+    *t32 = nullptr;
+  }
+  return e;
+}
+}  // namespace
+
+int hx_set_table_ex(hx_ctx* ctx, const double* table, int n_g, double d_inv_g, int which) {
+  if (!ctx) return HX_ERR_ARG;
+  if (which < HX_TABLE_BOTH || which > HX_TABLE_PRECONDITIONER) return fail(ctx, HX_ERR_ARG, "unknown table role");
+  if (!table || n_g < 2 || !(d_inv_g > 0)) return fail(ctx, HX_ERR_ARG, "need table, n_g >= 2, d_inv_g > 0");
+  for (int i = 0; i < 7 * n_g; ++i)
+    if (!std::isfinite(table[i])) return fail(ctx, HX_ERR_ARG, "table has non-finite entries");
+  if (which == HX_TABLE_PRECONDITIONER && !ctx->tab64)
+    return fail(ctx, HX_ERR_STATE, "set the operator table first");
+  cudaSetDevice(ctx->device);
+  double* t64 = nullptr;
+  float* t32 = nullptr;
+  cudaError_t e = upload_table(table, n_g, &t64, &t32);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "table upload");
-  ctx->table.assign(table, table + 7 * (size_t)n_g);
-  ctx->n_g = n_g;
-  ctx->d_inv_g = d_inv_g;
+  auto drop_precond = [&]() {
+    if (ctx->ptab64) cudaFree(ctx->ptab64);
+    if (ctx->ptab32) cudaFree(ctx->ptab32);
+    ctx->ptab64 = nullptr;
+    ctx->ptab32 = nullptr;
+  };
+  if (which == HX_TABLE_PRECONDITIONER) {
+    drop_precond();
+    ctx->ptab64 = t64;
+    ctx->ptab32 = t32;
+    ctx->pn_g = n_g;
+    ctx->pd_inv_g = d_inv_g;
+  } else {
+    if (which == HX_TABLE_OPERATOR && !ctx->ptab64 && ctx->tab64) {
+      // the preconditioner keeps the table it used so far
+      ctx->ptab64 = ctx->tab64;
+      ctx->ptab32 = ctx->tab32;
+      ctx->pn_g = ctx->n_g;
+      ctx->pd_inv_g = ctx->d_inv_g;
+    } else {
+      if (which == HX_TABLE_BOTH) drop_precond();
+      if (ctx->tab64 && ctx->tab64 != ctx->ptab64) cudaFree(ctx->tab64);
+      if (ctx->tab32 && ctx->tab32 != ctx->ptab32) cudaFree(ctx->tab32);
+    }
+    ctx->tab64 = t64;
+    ctx->tab32 = t32;
+    ctx->table.assign(table, table + 7 * (size_t)n_g);
+    ctx->n_g = n_g;
+    ctx->d_inv_g = d_inv_g;
+  }
   ctx->solvers.clear();
   ctx->solver_lru.clear();
   return HX_OK;
+}
+
+int hx_set_table(hx_ctx* ctx, const double* table, int n_g, double d_inv_g) {
+  return hx_set_table_ex(ctx, table, n_g, d_inv_g, HX_TABLE_BOTH);
 }
 
 int hx_apply_operator(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, double shift_beta,

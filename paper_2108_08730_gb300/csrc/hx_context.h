@@ -47,6 +47,11 @@ struct hx_ctx {
   std::vector<double> table;    // host copy [n_g][7]
   double* tab64 = nullptr;      // derived [n_g][kTabW]
   float* tab32 = nullptr;
+  // preconditioner table (hx_set_table_ex); NULL: the operator's table
+  double* ptab64 = nullptr;
+  float* ptab32 = nullptr;
+  int pn_g = 0;
+  double pd_inv_g = 0;
   int st32_cfg = -1;            // forced complex64 kernel configuration (-1: automatic)
   std::map<std::string, int> tuned;   // hx_autotune choices by grid size and nrhs
   // cached levels, keyed by their defining parameters
@@ -104,7 +109,7 @@ int check_grid(hx_ctx* ctx, const hx_grid* g);
 int get_level(hx_ctx* ctx, const hx_grid* g, const int n_level[3], double h_level, Level** out,
               double gamma_cap = 0.0);
 template <typename T>
-OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double beta);
+OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double beta, bool precond = false);
 
 // Profiler helpers: open/close an event pair around a launch of class `kind`
 // (no-ops when profiling is off); collect() folds finished pairs into the

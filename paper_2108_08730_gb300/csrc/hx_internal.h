@@ -24,6 +24,9 @@ int build_weight_table(const double* theta_deg, int n_theta, const double* phi_d
                        double inv_g_max, double d_inv_g, double lambda, double* out, int capacity,
                        int* n_g_out, std::string* err);
 
+int fit_joint_weights(const double* inv_g, int n, const double* theta_deg, int n_theta, const double* phi_deg,
+                      int n_phi, double* w7, std::string* err);
+
 // Per-level operator description handed to the kernels (device pointers).
 template <typename T>
 struct OpDesc {

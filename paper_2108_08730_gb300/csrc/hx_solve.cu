@@ -183,7 +183,7 @@ class Run {
 
   template <typename T>
   OpDesc<T> desc(int l, double beta) const {
-    OpDesc<T> d = make_desc<T>(ctx, *S->lvl[l], l == 0 ? v_fine : (const float*)S->vlev[l].p, beta);
+    OpDesc<T> d = make_desc<T>(ctx, *S->lvl[l], l == 0 ? v_fine : (const float*)S->vlev[l].p, beta, true);
     d.cfg32 = ctx_cfg32(ctx, S->n[l][0], S->n[l][1], S->n[l][2], S->R);
     return d;
   }
@@ -533,7 +533,7 @@ int setup_coarse_inverse(hx_ctx* ctx, SolverImpl* S, const float* /*v_fine*/, do
     double* coef = nullptr;
     e = cudaMalloc(&coef, (size_t)Nc * 54 * sizeof(double));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "coarse coefficients");
-    e = launch_row_coefficients(make_desc<double>(ctx, *S->lvl[L], (const float*)S->vlev[L].p, beta), coef, s);
+    e = launch_row_coefficients(make_desc<double>(ctx, *S->lvl[L], (const float*)S->vlev[L].p, beta, true), coef, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), coef, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(coef);
@@ -792,9 +792,9 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       cudaError_t e = S->acoef[l].alloc((size_t)27 * S->N[l] * cs);
       if (e == cudaSuccess) {
         if (l == 1)
-          e = prec == 64 ? launch_galerkin_onfly<double>(make_desc<double>(ctx, *S->lvl[0], v_dev, opt.shift_beta),
+          e = prec == 64 ? launch_galerkin_onfly<double>(make_desc<double>(ctx, *S->lvl[0], v_dev, opt.shift_beta, true),
                                                          S->acoef[1].p, S->n[1], stream)
-                         : launch_galerkin_onfly<float>(make_desc<float>(ctx, *S->lvl[0], v_dev, opt.shift_beta),
+                         : launch_galerkin_onfly<float>(make_desc<float>(ctx, *S->lvl[0], v_dev, opt.shift_beta, true),
                                                         S->acoef[1].p, S->n[1], stream);
         else
           e = prec == 64 ? launch_galerkin_stored<double>(S->acoef[l - 1].p, S->n[l - 1], S->acoef[l].p, S->n[l], stream)

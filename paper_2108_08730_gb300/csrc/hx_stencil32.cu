@@ -95,9 +95,17 @@ struct I {
 };
 
 // ------------------------------------------------------------ configuration
-// HX_ST32_PREFETCH = 0 turns the one-plane-ahead table fetch off.
+// HX_ST32_PREFETCH = 0 turns the one-plane-ahead table fetch off;
+// HX_ST32_MINB sets the resident CTAs per SM the register budget is cut for;
+// HX_ST32_ZMAX > 0 caps the z-chunk of a CTA.
 #ifndef HX_ST32_PREFETCH
 #define HX_ST32_PREFETCH 1
+#endif
+#ifndef HX_ST32_MINB
+#define HX_ST32_MINB 2
+#endif
+#ifndef HX_ST32_ZMAX
+#define HX_ST32_ZMAX 0
 #endif
 constexpr int kW = 32;              // tile extent in x: one warp
 constexpr int kNW = 8;              // warps per CTA
@@ -115,7 +123,7 @@ struct Cfg {
   static constexpr int D = SLOTB <= 6144 ? 5 : 4;      // planes in flight beyond the window
   static constexpr int NSLOT = D + 3;
   static constexpr int SMEM = NSLOT * SLOTB;
-  static constexpr int MINB = 2;                       // resident CTAs per SM
+  static constexpr int MINB = HX_ST32_MINB;            // resident CTAs per SM
   // with RB >= 4 the table lookup is amortised over the fields and its
   // registers are better spent on the class-sum window
   static constexpr bool PREFETCH = HX_ST32_PREFETCH && RB <= 2;
@@ -513,7 +521,8 @@ cudaError_t launch_cfg(const OpDesc<float>& op, const void* x, const void* b, vo
   }
   const int bx = (op.nx + kW - 1) / kW, by = (op.ny + K::TY - 1) / K::TY;
   const int nrb = (nrhs + RB - 1) / RB;
-  const int zchunk = pick_zchunk32(op.nz, (long long)bx * by, nrb, g_num_sms * K::MINB, K::D + 2);
+  int zchunk = pick_zchunk32(op.nz, (long long)bx * by, nrb, g_num_sms * K::MINB, K::D + 2);
+  if (HX_ST32_ZMAX > 0 && zchunk > HX_ST32_ZMAX) zchunk = (op.nz + (op.nz + HX_ST32_ZMAX - 1) / HX_ST32_ZMAX - 1) / ((op.nz + HX_ST32_ZMAX - 1) / HX_ST32_ZMAX);
   const long long gz = (long long)((op.nz + zchunk - 1) / zchunk) * nrb;
   if (gz > 65535) return cudaErrorInvalidConfiguration;
   kern<<<dim3(bx, by, (unsigned)gz), kThr, K::SMEM, s>>>(op, (const float2*)x, (const float2*)b,

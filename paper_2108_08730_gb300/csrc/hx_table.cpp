@@ -8,6 +8,7 @@
 // i+1, so the triangular factor R of a Givens QR stays inside a band of width
 // 10.  Rows are rotated into R one at a time (numerically orthogonal, no
 // normal equations), then R w = Q^T b is back-substituted.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -153,6 +154,92 @@ int build_weight_table(const double* theta_deg, int n_theta, const double* phi_d
     o[5] = wm3;
     o[6] = (1.0 - wm1 - 6.0 * wm2 - 12.0 * wm3) / 8.0;       // Eq. eqswm, per point
   }
+  return HX_OK;
+}
+
+// Non-adaptive weights (Eq. eq_cost): one weight vector for the plane waves
+// of every listed 1/G at once -- the G4 stencil for {1/4}, Gm for
+// {1/4, 1/6, 1/8, 1/10}.  Minimum-norm least squares through the normal
+// matrix N = H^T H (5 x 5): cyclic Jacobi eigen-decomposition, then
+// w = V diag(1/d_k, d_k > 1e-12 max d) V^T H^T g.  A single G gives a rank-3
+// H (all five H_l vanish on a plane through (A, B, C) = (1, 3, 3)), so the
+// minimum-norm choice matters there.
+int fit_joint_weights(const double* inv_g, int n, const double* theta_deg, int n_theta, const double* phi_deg,
+                      int n_phi, double* w7, std::string* err) {
+  if (!inv_g || n < 1 || !theta_deg || !phi_deg || n_theta < 1 || n_phi < 1 || !w7) {
+    *err = "need 1/G values, angle lists and an output";
+    return HX_ERR_ARG;
+  }
+  double N[5][5] = {}, hg[5] = {};
+  for (int q = 0; q < n; ++q) {
+    if (!(inv_g[q] > 0.0) || !(inv_g[q] <= 0.5)) {
+      *err = "1/G values must lie in (0, 0.5]";
+      return HX_ERR_ARG;
+    }
+    for (int p = 0; p < n_phi; ++p)
+      for (int t = 0; t < n_theta; ++t) {
+        double H[5], g;
+        linear_row(inv_g[q], theta_deg[t] * M_PI / 180.0, phi_deg[p] * M_PI / 180.0, H, &g);
+        for (int a = 0; a < 5; ++a) {
+          hg[a] += H[a] * g;
+          for (int b = 0; b < 5; ++b) N[a][b] += H[a] * H[b];
+        }
+      }
+  }
+  // cyclic Jacobi: N = V diag(d) V^T
+  double V[5][5] = {};
+  for (int a = 0; a < 5; ++a) V[a][a] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; b < 5; ++b) {
+        tot += N[a][b] * N[a][b];
+        if (a != b) off += N[a][b] * N[a][b];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < 4; ++p)
+      for (int q = p + 1; q < 5; ++q) {
+        if (N[p][q] == 0.0) continue;
+        const double theta = (N[q][q] - N[p][p]) / (2.0 * N[p][q]);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < 5; ++k) {      // N <- N J
+          const double nkp = N[k][p], nkq = N[k][q];
+          N[k][p] = c * nkp - s * nkq;
+          N[k][q] = s * nkp + c * nkq;
+        }
+        for (int k = 0; k < 5; ++k) {      // N <- J^T N
+          const double npk = N[p][k], nqk = N[q][k];
+          N[p][k] = c * npk - s * nqk;
+          N[q][k] = s * npk + c * nqk;
+        }
+        for (int k = 0; k < 5; ++k) {      // V <- V J
+          const double vkp = V[k][p], vkq = V[k][q];
+          V[k][p] = c * vkp - s * vkq;
+          V[k][q] = s * vkp + c * vkq;
+        }
+      }
+  }
+  double dmax = 0.0;
+  for (int a = 0; a < 5; ++a) dmax = std::max(dmax, N[a][a]);
+  if (!(dmax > 0.0) || !std::isfinite(dmax)) {
+    *err = "degenerate joint fit";
+    return HX_ERR_NUMERIC;
+  }
+  double w[5] = {};
+  for (int k = 0; k < 5; ++k) {
+    if (!(N[k][k] > 1e-12 * dmax)) continue;
+    double proj = 0.0;
+    for (int a = 0; a < 5; ++a) proj += V[a][k] * hg[a];
+    for (int a = 0; a < 5; ++a) w[a] += V[a][k] * proj / N[k][k];
+  }
+  w7[0] = w[0];
+  w7[1] = w[1];
+  w7[2] = 1.0 - w[0] - w[1];
+  w7[3] = w[2];
+  w7[4] = w[3];
+  w7[5] = w[4];
+  w7[6] = (1.0 - w[2] - 6.0 * w[3] - 12.0 * w[4]) / 8.0;
   return HX_OK;
 }
 

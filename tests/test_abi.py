@@ -83,3 +83,15 @@ def test_ctx_create_without_gpu_fails_cleanly():
         pytest.skip("GPU present")
     with pytest.raises(B.HxError):
         B.Context(0)
+
+
+@pytest.mark.parametrize("inv_g", [[0.25], [0.25, 1 / 6, 1 / 8, 0.1]])
+def test_joint_fit_matches_oracle(inv_g):
+    # the non-adaptive G4 / Gm weights (Eq. eq_cost): library normal-matrix
+    # eigen-solve vs the oracle's SVD least squares (minimum norm for G4)
+    from oracle import weights as W
+    w7 = B.fit_joint_weights(inv_g)
+    ref = W.expand_weights(W.fit_joint(inv_g).reshape(1, 5))[0]
+    assert np.max(np.abs(w7 - ref)) < 1e-7
+    assert abs(w7[0] + w7[1] + w7[2] - 1) < 1e-14
+    assert abs(w7[3] + 6 * w7[4] + 12 * w7[5] + 8 * w7[6] - 1) < 1e-14

@@ -270,3 +270,26 @@ def test_apply_batched_replays_in_a_cuda_graph(ctx, otable):
         torch.cuda.synchronize()
         for y, w in zip(ys, want):
             assert torch.equal(y, w)
+
+
+def test_operator_table_role_changes_only_the_operator(ctx, otable):
+    # hx_set_table_ex(..., HX_TABLE_OPERATOR): applies use the new table
+    nodes, T = otable
+    v, A, g = _problem(3, 0.0, otable)
+    w7 = B.fit_joint_weights([0.25])
+    fixed = B.fixed_table(w7, len(nodes))
+    c = B.Context(0, table=T)
+    c.set_table(fixed, role="operator")
+    shape, h, f, npml, vmin, vmax = CASES[3]
+    prof = O.profiles_for(shape, h, npml, vmax, 1e-3)
+    Af = O.assemble_csr(v, h, f, prof, fixed, nodes)
+    x = synth.random_field(shape, 1, 123)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.empty_like(xd)
+    c.apply(g, torch.from_numpy(v).cuda(), xd, yd)
+    torch.cuda.synchronize()
+    xr = x.reshape(1, -1)
+    ref = (Af @ xr.T).T
+    bound = (abs(Af) @ np.abs(xr).T).T
+    assert np.max(np.abs(yd.cpu().numpy().reshape(1, -1) - ref) / bound) <= TOL[64]
+    c.close()
