@@ -156,3 +156,35 @@ def test_profiler_counts_fine_level_kernels(ctx):
     assert p["apply32"][0] == 2 * rep["inner_iters"]
     assert p["apply32"][1] > 0 and p["apply32"][2] == p["apply32"][0] * (16 * wl.n_points + 4 * wl.n_points)
     assert p["all"][0] > p["apply32"][0] + p["smooth32"][0]
+
+
+def test_time_limit_stops_a_solve_with_its_best_iterate(ctx):
+    # hx_solve_opts.time_limit_s: a deadline checked where the host
+    # synchronises; an unreachable tolerance makes the solve run into it
+    wl = synth.linear_gradient(n=61, npml=8)
+    out = torch.zeros((1,) + wl.shape, dtype=torch.complex128, device="cuda")
+    import time
+    t0 = time.perf_counter()
+    rep = ctx.solve(B.grid_of(wl), torch.from_numpy(wl.v).cuda(), B.sources_of(wl), 1, out,
+                    check=False, tol=1e-30, max_outer=1000, time_limit_s=0.5)
+    el = time.perf_counter() - t0
+    assert rep["status"] == -3                                   # HX_ERR_NOT_CONVERGED
+    assert el < 10.0
+    assert 0 < rep["rel_residual"] < 1e-6                        # the refinement did progress
+    assert torch.isfinite(torch.view_as_real(out)).all()
+
+
+def test_autotune_option_records_a_configuration(ctx):
+    # hx_solve tunes the complex64 kernel once per (grid size, nrhs) above
+    # 2^20 point*RHS; the solve converges the same either way
+    wl = synth.linear_gradient(n=64, npml=8)
+    g = B.grid_of(wl)
+    vd = torch.from_numpy(wl.v).cuda()
+    src = [(s[0], s[1], s[2], r, 1.0) for r, s in enumerate([wl.sources[0]] * 4)]
+    outs = []
+    for tune in (0, 1):
+        out = torch.zeros((4,) + wl.shape, dtype=torch.complex128, device="cuda")
+        rep = ctx.solve(g, vd, src, 4, out, autotune=tune)
+        assert rep["status"] == 0
+        outs.append(out)
+    assert torch.linalg.vector_norm(outs[0] - outs[1]) <= 1e-6 * torch.linalg.vector_norm(outs[0])
