@@ -341,10 +341,26 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
         err = float(torch.linalg.vector_norm(mixed - ref) / torch.linalg.vector_norm(ref))
+        # the FP64 form's own dominant kernel class, timed per launch in a second solve
+        ctx.profile(True)
+        ctx.solve(g, vd, src, R, torch.zeros_like(ref), mode=B.SOLVE_FP64, tol=1e-12, max_iter=20000,
+                  check=False)
+        p64 = {k: v for k, v in ctx.profile_read().items() if k in ("apply64", "smooth64") and v[0] > 0}
+        ctx.profile(False)
+        roof64 = None
+        if p64:
+            k64 = max(p64, key=lambda k: p64[k][1])
+            n64, ms64, by64 = p64[k64]
+            peak = (_peaks() or {}).get("hbm_gbs", 6800.0)
+            roof64 = {"kernel": {"apply64": "stencil_kernel<double, kApply>",
+                                 "smooth64": "stencil_kernel<double, kJacobi|kResidual>"}[k64],
+                      "achieved_gbs": round(by64 / (ms64 / 1e3) / 1e9, 1), "frac_of_hbm": round(by64 / (ms64 / 1e3) / 1e9 / peak, 4),
+                      "bound": "FP64 ALU (GB300 runs FP64 at a small fraction of its FP32 rate)"}
         acc = {"rel_l2_mixed_vs_fp64": err, "fp64_status": rep64["status"],
                "fp64_rel_residual": rep64["rel_residual"], "fp64_iters": rep64["inner_iters"],
                "fp64_value": round(units / t64 / 1e6, 4), "fp64_unit": UNIT,
-               "speedup_mixed_vs_fp64": round(value / world / (units / t64 / 1e6), 2)}
+               "speedup_mixed_vs_fp64": round(value / world / (units / t64 / 1e6), 2),
+               "fp64_dominant_kernel": roof64}
 
     # ---- roofline of the dominant kernel class
     peaks = _peaks()
