@@ -26,6 +26,11 @@
  *    thread.
  *  - Every call returns an hx_status; on failure it also records a message
  *    retrievable with hx_last_error.  Nothing throws across the ABI.
+ *  - Kernels are launched with programmatic dependent launch: a kernel's
+ *    CTAs may become resident while its predecessor on the same stream
+ *    drains, and wait for it in hardware before touching memory.  Setting
+ *    the environment variable HX_PDL=0 before the first launch turns this
+ *    off (results are bit-identical either way).
  */
 #ifndef HX27_H
 #define HX27_H

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -167,6 +168,13 @@ std::atomic<long long> g_launches{0};
 }
 long long launch_count() { return g_launches.load(); }
 void count_launch(int n) { g_launches += n; }
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("HX_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 
 cudaEvent_t prof_begin(hx_ctx* ctx, cudaStream_t s) {
   if (!ctx->prof_on) return nullptr;

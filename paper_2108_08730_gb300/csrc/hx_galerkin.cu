@@ -11,6 +11,7 @@
 #include "hx_complex.cuh"
 #include "hx_galerkin.cuh"
 #include "hx_internal.h"
+#include "hx_launch.cuh"
 
 namespace hx {
 namespace {
@@ -66,6 +67,7 @@ template <typename T, bool ONFLY>
 __global__ void __launch_bounds__(128)
 galerkin_k(OpDesc<T> op, const typename CT<T>::type* __restrict__ cf, int fx, int fy, int fz,
            typename CT<T>::type* __restrict__ cc, int cx, int cy, int cz) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const long long Nc = (long long)cx * cy * cz, Nf = (long long)fx * fy * fz;
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < Nc;
@@ -117,6 +119,7 @@ __global__ void __launch_bounds__(256)
 stored_stencil_k(const typename CT<T>::type* __restrict__ coef, int nx, int ny, int nz,
                  const typename CT<T>::type* __restrict__ x, const typename CT<T>::type* __restrict__ b,
                  typename CT<T>::type* __restrict__ y, int R, T omega_j) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const long long N = (long long)nx * ny * nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -156,6 +159,7 @@ __global__ void __launch_bounds__(128)
 direct_stencil_k(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
                  const typename CT<T>::type* __restrict__ b, typename CT<T>::type* __restrict__ y,
                  int R, T omega_j) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const long long N = (long long)op.nx * op.ny * op.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -201,7 +205,7 @@ cudaError_t launch_galerkin_onfly(const OpDesc<T>& fine, void* coarse_coef, cons
                                   cudaStream_t s) {
   using C = typename CT<T>::type;
   const long long Nc = (long long)nc[0] * nc[1] * nc[2];
-  galerkin_k<T, true><<<blocks_for(Nc, 128, 152 * 64), 128, 0, s>>>(
+  (void)launch_k(galerkin_k<T, true>, blocks_for(Nc, 128, 152 * 64), 128, 0, s,
       fine, nullptr, fine.nx, fine.ny, fine.nz, (C*)coarse_coef, nc[0], nc[1], nc[2]);
   count_launch(1);
   return cudaGetLastError();
@@ -213,7 +217,7 @@ cudaError_t launch_galerkin_stored(const void* fine_coef, const int nf[3], void*
   using C = typename CT<T>::type;
   const long long Nc = (long long)nc[0] * nc[1] * nc[2];
   OpDesc<T> dummy{};
-  galerkin_k<T, false><<<blocks_for(Nc, 128, 152 * 64), 128, 0, s>>>(
+  (void)launch_k(galerkin_k<T, false>, blocks_for(Nc, 128, 152 * 64), 128, 0, s,
       dummy, (const C*)fine_coef, nf[0], nf[1], nf[2], (C*)coarse_coef, nc[0], nc[1], nc[2]);
   count_launch(1);
   return cudaGetLastError();
@@ -227,19 +231,19 @@ cudaError_t launch_stored_stencil(const void* coef, const int n[3], int mode, co
   const unsigned g = blocks_for(N, 256, 152 * 16);
   switch (mode) {
     case kApply:
-      stored_stencil_k<T, kApply><<<g, 256, 0, s>>>((const C*)coef, n[0], n[1], n[2], (const C*)x,
+      (void)launch_k(stored_stencil_k<T, kApply>, g, 256, 0, s, (const C*)coef, n[0], n[1], n[2], (const C*)x,
                                                     (const C*)b, (C*)y, R, (T)omega_j);
       break;
     case kResidual:
-      stored_stencil_k<T, kResidual><<<g, 256, 0, s>>>((const C*)coef, n[0], n[1], n[2], (const C*)x,
+      (void)launch_k(stored_stencil_k<T, kResidual>, g, 256, 0, s, (const C*)coef, n[0], n[1], n[2], (const C*)x,
                                                        (const C*)b, (C*)y, R, (T)omega_j);
       break;
     case kJacobi:
-      stored_stencil_k<T, kJacobi><<<g, 256, 0, s>>>((const C*)coef, n[0], n[1], n[2], (const C*)x,
+      (void)launch_k(stored_stencil_k<T, kJacobi>, g, 256, 0, s, (const C*)coef, n[0], n[1], n[2], (const C*)x,
                                                      (const C*)b, (C*)y, R, (T)omega_j);
       break;
     case kJacobi0:
-      stored_stencil_k<T, kJacobi0><<<g, 256, 0, s>>>((const C*)coef, n[0], n[1], n[2], (const C*)x,
+      (void)launch_k(stored_stencil_k<T, kJacobi0>, g, 256, 0, s, (const C*)coef, n[0], n[1], n[2], (const C*)x,
                                                       (const C*)b, (C*)y, R, (T)omega_j);
       break;
     default:
@@ -257,10 +261,10 @@ cudaError_t launch_direct_stencil(const OpDesc<T>& op, int mode, const void* x, 
   const unsigned g = blocks_for(N, 128, 152 * 32);
   const T om = (T)omega_j;
   switch (mode) {
-    case kApply: direct_stencil_k<T, kApply><<<g, 128, 0, s>>>(op, (const C*)x, (const C*)b, (C*)y, R, om); break;
-    case kResidual: direct_stencil_k<T, kResidual><<<g, 128, 0, s>>>(op, (const C*)x, (const C*)b, (C*)y, R, om); break;
-    case kJacobi: direct_stencil_k<T, kJacobi><<<g, 128, 0, s>>>(op, (const C*)x, (const C*)b, (C*)y, R, om); break;
-    case kJacobi0: direct_stencil_k<T, kJacobi0><<<g, 128, 0, s>>>(op, (const C*)x, (const C*)b, (C*)y, R, om); break;
+    case kApply: (void)launch_k(direct_stencil_k<T, kApply>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om); break;
+    case kResidual: (void)launch_k(direct_stencil_k<T, kResidual>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om); break;
+    case kJacobi: (void)launch_k(direct_stencil_k<T, kJacobi>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om); break;
+    case kJacobi0: (void)launch_k(direct_stencil_k<T, kJacobi0>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om); break;
     default: return cudaErrorInvalidValue;
   }
   count_launch(1);

@@ -23,6 +23,7 @@
 #include "hx_context.h"
 #include "hx_galerkin.cuh"
 #include "hx_internal.h"
+#include "hx_launch.cuh"
 #include "hx_vec.cuh"
 
 namespace hx {
@@ -132,6 +133,7 @@ int plan_levels(const int n0[3], int requested, int out[kMaxLev][3]) {
 }
 
 __global__ void minmax_k(const float* __restrict__ v, long long N, float* part) {
+  pdl_enter();
   float lo = 3.0e38f, hi = -3.0e38f, bad = 0.f;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
@@ -161,6 +163,7 @@ __global__ void minmax_k(const float* __restrict__ v, long long N, float* part) 
 }
 
 __global__ void init_scalars_k(double2* rho, double2* alpha, double2* omega, int* brk, int R) {
+  pdl_enter();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   rho[r] = make_double2(1.0, 0.0);
@@ -374,7 +377,7 @@ class Run {
     HX_CK(cudaMemsetAsync(x, 0, fb, stream));
     HX_CK(cudaMemsetAsync(p, 0, fb, stream));
     HX_CK(cudaMemsetAsync(v, 0, fb, stream));
-    init_scalars_k<<<(R + 127) / 128, 128, 0, stream>>>(S->rho, S->alpha, S->omega, S->brk, R);
+    (void)launch_k(init_scalars_k, (R + 127) / 128, 128, 0, stream, S->rho, S->alpha, S->omega, S->brk, R);
     count_launch(1);
     HX_CK(cudaGetLastError());
     S->h_active = active_in;
@@ -462,7 +465,7 @@ int validate_velocity(hx_ctx* ctx, const hx_grid* g, const float* v, cudaStream_
   float* part = nullptr;
   cudaError_t e = cudaMalloc(&part, 3 * nb * sizeof(float));
   if (e != cudaSuccess) return cuda_fail(ctx, e, "validation buffer");
-  minmax_k<<<nb, 256, 0, s>>>(v, N, part);
+  (void)launch_k(minmax_k, nb, 256, 0, s, v, N, part);
   count_launch(1);
   std::vector<float> h(3 * nb);
   e = cudaGetLastError();

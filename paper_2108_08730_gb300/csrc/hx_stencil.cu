@@ -27,6 +27,7 @@
 
 #include "hx_complex.cuh"
 #include "hx_internal.h"
+#include "hx_launch.cuh"
 
 namespace hx {
 namespace {
@@ -126,6 +127,7 @@ __global__ void __launch_bounds__(kTX * kTY, sizeof(T) == 4 ? 3 : 2)
 stencil_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
                const typename CT<T>::type* __restrict__ b, typename CT<T>::type* __restrict__ y,
                int nrhs, long long rstride, int zchunk, T omega_j) {
+  pdl_enter();
   using C = typename CT<T>::type;
   constexpr int TX = kTX, TY = kTY, PW = kPW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -397,6 +399,7 @@ template <typename T, bool SHIFT>
 __global__ void jacobi0_kernel(OpDesc<T> op, const typename CT<T>::type* __restrict__ b,
                                typename CT<T>::type* __restrict__ y, int nrhs, long long rstride,
                                T omega_j) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const long long N = (long long)op.nx * op.ny * op.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
@@ -420,6 +423,7 @@ __global__ void jacobi0_kernel(OpDesc<T> op, const typename CT<T>::type* __restr
 
 // One thread per row: the 27 coefficients in (dk, dj, di) order, FP64.
 __global__ void row_coef_kernel(OpDesc<double> op, double2* __restrict__ coef) {
+  pdl_enter();
   const long long N = (long long)op.nx * op.ny * op.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
@@ -502,7 +506,7 @@ cudaError_t launch_t(const OpDesc<T>& op, const void* x, const void* b, void* y,
   const long long gz = (long long)nzc * nrb;
   if (gz > 65535) return cudaErrorInvalidConfiguration;
   dim3 grid(bx, by, (unsigned)gz), block(kTX, kTY);
-  kern<<<grid, block, smem, s>>>(op, (const C*)x, (const C*)b, (C*)y, nrhs, rstride, zchunk, (T)omega_j);
+  (void)launch_k(kern, grid, block, smem, s, op, (const C*)x, (const C*)b, (C*)y, nrhs, rstride, zchunk, (T)omega_j);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -515,9 +519,9 @@ cudaError_t launch_j0(const OpDesc<T>& op, const void* b, void* y, int nrhs, lon
   long long blocks = (N + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (op.beta != 0)
-    jacobi0_kernel<T, true><<<(unsigned)blocks, 256, 0, s>>>(op, (const C*)b, (C*)y, nrhs, rstride, (T)omega_j);
+    (void)launch_k(jacobi0_kernel<T, true>, (unsigned)blocks, 256, 0, s, op, (const C*)b, (C*)y, nrhs, rstride, (T)omega_j);
   else
-    jacobi0_kernel<T, false><<<(unsigned)blocks, 256, 0, s>>>(op, (const C*)b, (C*)y, nrhs, rstride, (T)omega_j);
+    (void)launch_k(jacobi0_kernel<T, false>, (unsigned)blocks, 256, 0, s, op, (const C*)b, (C*)y, nrhs, rstride, (T)omega_j);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -563,7 +567,7 @@ cudaError_t launch_row_coefficients(const OpDesc<double>& op, double* coef, cuda
   const long long N = (long long)op.nx * op.ny * op.nz;
   long long blocks = (N + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  row_coef_kernel<<<(unsigned)blocks, 256, 0, s>>>(op, (double2*)coef);
+  (void)launch_k(row_coef_kernel, (unsigned)blocks, 256, 0, s, op, (double2*)coef);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -27,6 +27,7 @@
 
 #include "hx_complex.cuh"
 #include "hx_internal.h"
+#include "hx_launch.cuh"
 
 namespace hx {
 namespace {
@@ -449,6 +450,7 @@ template <int MODE, int YB, int RB>
 __global__ void __launch_bounds__(kThr, Cfg<YB, RB>::MINB)
 st32_kernel(const OpDesc<float> op, const float2* __restrict__ x, const float2* __restrict__ b,
             float2* __restrict__ y, int nrhs, long long rstride, int zchunk, float omega_j) {
+  pdl_enter();
   extern __shared__ __align__(16) float2 ring[];       // [NSLOT][RB][PH][kPW]
   st32_tile<MODE, YB, RB>(op, x, b, y, nrhs, rstride, zchunk, omega_j, blockIdx.x, blockIdx.y, blockIdx.z, ring);
 }
@@ -460,6 +462,7 @@ template <int YB, int RB>
 __global__ void __launch_bounds__(kThr, Cfg<YB, RB>::MINB)
 st32_group_kernel(const GroupProb* __restrict__ probs, const GroupItem* __restrict__ items, int nitems,
                   int* __restrict__ counter) {
+  pdl_enter();
   extern __shared__ __align__(16) float2 ring[];
   __shared__ int next;
   __shared__ GroupProb P;                              // the current item's problem
@@ -525,7 +528,7 @@ cudaError_t launch_cfg(const OpDesc<float>& op, const void* x, const void* b, vo
   if (HX_ST32_ZMAX > 0 && zchunk > HX_ST32_ZMAX) zchunk = (op.nz + (op.nz + HX_ST32_ZMAX - 1) / HX_ST32_ZMAX - 1) / ((op.nz + HX_ST32_ZMAX - 1) / HX_ST32_ZMAX);
   const long long gz = (long long)((op.nz + zchunk - 1) / zchunk) * nrb;
   if (gz > 65535) return cudaErrorInvalidConfiguration;
-  kern<<<dim3(bx, by, (unsigned)gz), kThr, K::SMEM, s>>>(op, (const float2*)x, (const float2*)b,
+  (void)launch_k(kern, dim3(bx, by, (unsigned)gz), kThr, K::SMEM, s, op, (const float2*)x, (const float2*)b,
                                                           (float2*)y, nrhs, rstride, zchunk,
                                                           (float)omega_j);
   count_launch(1);
@@ -571,7 +574,7 @@ cudaError_t launch_group_cfg(const GroupProb* probs_dev, const GroupItem* items_
     if (cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) g_num_sms = 152;
   }
   const int grid = std::min(nitems, g_num_sms * K::MINB);
-  kern<<<grid, kThr, K::SMEM, s>>>(probs_dev, items_dev, nitems, counter);
+  (void)launch_k(kern, grid, kThr, K::SMEM, s, probs_dev, items_dev, nitems, counter);
   count_launch(1);
   return cudaGetLastError();
 }

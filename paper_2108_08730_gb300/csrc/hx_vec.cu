@@ -1,6 +1,7 @@
 // Batched vector kernels of the solver (see hx_vec.cuh).
 #include "hx_complex.cuh"
 #include "hx_internal.h"
+#include "hx_launch.cuh"
 #include "hx_vec.cuh"
 
 namespace hx {
@@ -47,6 +48,7 @@ template <typename T, bool NORM>
 __global__ void __launch_bounds__(kThreads)
 dot_partial(const typename CT<T>::type* __restrict__ a, const typename CT<T>::type* __restrict__ b,
             long long N, double2* __restrict__ part) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const int r = blockIdx.y;
   const C* ar = a + (long long)r * N;
@@ -69,6 +71,7 @@ dot_partial(const typename CT<T>::type* __restrict__ a, const typename CT<T>::ty
 
 __global__ void __launch_bounds__(kThreads)
 dot_finish(const double2* __restrict__ part, int nblk, double2* out, double* out_re) {
+  pdl_enter();
   const int r = blockIdx.x;
   double2 s = make_double2(0.0, 0.0);
   for (int i = threadIdx.x; i < nblk; i += kThreads) {
@@ -87,6 +90,7 @@ template <typename T>
 __global__ void bicg_p_k(typename CT<T>::type* __restrict__ p, const typename CT<T>::type* __restrict__ r,
                          const typename CT<T>::type* __restrict__ v, const double2* beta,
                          const double2* omega, long long N) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const int k = blockIdx.y;
   const C be = from_d2<C>(beta[k]), om = from_d2<C>(omega[k]);
@@ -102,6 +106,7 @@ __global__ void bicg_p_k(typename CT<T>::type* __restrict__ p, const typename CT
 template <typename T>
 __global__ void bicg_s_k(typename CT<T>::type* __restrict__ sv, const typename CT<T>::type* __restrict__ r,
                          const typename CT<T>::type* __restrict__ v, const double2* alpha, long long N) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const int k = blockIdx.y;
   const C al = from_d2<C>(alpha[k]);
@@ -119,6 +124,7 @@ __global__ void bicg_xr_k(typename CT<T>::type* __restrict__ x, typename CT<T>::
                           const typename CT<T>::type* __restrict__ sh,
                           const typename CT<T>::type* __restrict__ t, const double2* alpha,
                           const double2* omega, long long N) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const int k = blockIdx.y;
   const C al = from_d2<C>(alpha[k]), om = from_d2<C>(omega[k]);
@@ -136,6 +142,7 @@ __global__ void bicg_xr_k(typename CT<T>::type* __restrict__ x, typename CT<T>::
 template <typename T>
 __global__ void restrict_k(const typename CT<T>::type* __restrict__ f, int fx, int fy, int fz,
                            typename CT<T>::type* __restrict__ c, int cx, int cy, int cz) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const long long Nc = (long long)cx * cy * cz, Nf = (long long)fx * fy * fz;
   const int r = blockIdx.y;
@@ -165,6 +172,7 @@ __global__ void restrict_k(const typename CT<T>::type* __restrict__ f, int fx, i
 template <typename T>
 __global__ void prolong_k(typename CT<T>::type* __restrict__ f, int fx, int fy, int fz,
                           const typename CT<T>::type* __restrict__ c, int cx, int cy, int cz) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const long long Nc = (long long)cx * cy * cz, Nf = (long long)fx * fy * fz;
   const int r = blockIdx.y;
@@ -198,6 +206,7 @@ __global__ void prolong_k(typename CT<T>::type* __restrict__ f, int fx, int fy, 
 
 __global__ void inject_v_k(const float* __restrict__ vf, int fx, int fy, float* __restrict__ vc,
                            int cx, int cy, int cz) {
+  pdl_enter();
   const long long Nc = (long long)cx * cy * cz;
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < Nc;
        I += (long long)gridDim.x * blockDim.x) {
@@ -208,6 +217,7 @@ __global__ void inject_v_k(const float* __restrict__ vf, int fx, int fy, float* 
 
 __global__ void cast_scale_k(const double2* __restrict__ r64, float2* __restrict__ r32,
                              const double* scale, long long N) {
+  pdl_enter();
   const int k = blockIdx.y;
   const double s = scale[k];
   const long long o = (long long)k * N;
@@ -221,6 +231,7 @@ __global__ void cast_scale_k(const double2* __restrict__ r64, float2* __restrict
 template <class D>
 __global__ void axpy_mixed_k(double2* __restrict__ x, const D* __restrict__ d,
                              const double* scale, long long N) {
+  pdl_enter();
   const int k = blockIdx.y;
   const double s = scale[k];
   const long long o = (long long)k * N;
@@ -236,6 +247,7 @@ __global__ void axpy_mixed_k(double2* __restrict__ x, const D* __restrict__ d,
 
 template <typename T>
 __global__ void add_sources_k(typename CT<T>::type* r, long long N, const SourceEntry* e, int n) {
+  pdl_enter();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
     T* p = (T*)(r + (long long)e[k].rhs * N + e[k].idx);
     atomicAdd(p, (T)e[k].re);
@@ -251,6 +263,7 @@ __device__ __forceinline__ bool tiny(double2 a) { return !(a.x * a.x + a.y * a.y
 
 __global__ void scal_beta_k(double2* beta, double2* rho, const double2* rho_new, const double2* alpha,
                             const double2* omega, const int* active, int* brk, int R) {
+  pdl_enter();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   if (!active[r]) { beta[r] = make_double2(0, 0); return; }
@@ -261,6 +274,7 @@ __global__ void scal_beta_k(double2* beta, double2* rho, const double2* rho_new,
 
 __global__ void scal_alpha_k(double2* alpha, const double2* rho, const double2* rv, int* active,
                              int* brk, int R) {
+  pdl_enter();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   if (!active[r]) { alpha[r] = make_double2(0, 0); return; }
@@ -270,6 +284,7 @@ __global__ void scal_alpha_k(double2* alpha, const double2* rho, const double2* 
 
 __global__ void scal_omega_k(double2* omega, const double2* ts, const double* tt, int* active,
                              int* brk, int R) {
+  pdl_enter();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   if (!active[r]) { omega[r] = make_double2(0, 0); return; }
@@ -281,6 +296,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 dense_matvec_k(const typename CT<T>::type* __restrict__ M, const typename CT<T>::type* __restrict__ b,
                typename CT<T>::type* __restrict__ out, long long n) {
+  pdl_enter();
   using C = typename CT<T>::type;
   const long long i = blockIdx.x;
   const int r = blockIdx.y;
@@ -302,7 +318,7 @@ template <typename T>
 cudaError_t launch_dense_matvec(const void* M, const void* b, void* out, long long n, int R,
                                 cudaStream_t s) {
   using C = typename CT<T>::type;
-  dense_matvec_k<T><<<dim3((unsigned)n, R), kThreads, 0, s>>>((const C*)M, (const C*)b, (C*)out, n);
+  (void)launch_k(dense_matvec_k<T>, dim3((unsigned)n, R), kThreads, 0, s, (const C*)M, (const C*)b, (C*)out, n);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -321,8 +337,8 @@ cudaError_t launch_dot(const void* a, const void* b, long long N, int R, double2
                        cudaStream_t s) {
   using C = typename CT<T>::type;
   const int nb = reduce_blocks(N);
-  dot_partial<T, false><<<dim3(nb, R), kThreads, 0, s>>>((const C*)a, (const C*)b, N, part);
-  dot_finish<<<R, kThreads, 0, s>>>(part, nb, out, nullptr);
+  (void)launch_k(dot_partial<T, false>, dim3(nb, R), kThreads, 0, s, (const C*)a, (const C*)b, N, part);
+  (void)launch_k(dot_finish, R, kThreads, 0, s, part, nb, out, nullptr);
   count_launch(2);
   return cudaGetLastError();
 }
@@ -331,8 +347,8 @@ template <typename T>
 cudaError_t launch_norm2(const void* a, long long N, int R, double2* part, double* out, cudaStream_t s) {
   using C = typename CT<T>::type;
   const int nb = reduce_blocks(N);
-  dot_partial<T, true><<<dim3(nb, R), kThreads, 0, s>>>((const C*)a, (const C*)a, N, part);
-  dot_finish<<<R, kThreads, 0, s>>>(part, nb, nullptr, out);
+  (void)launch_k(dot_partial<T, true>, dim3(nb, R), kThreads, 0, s, (const C*)a, (const C*)a, N, part);
+  (void)launch_k(dot_finish, R, kThreads, 0, s, part, nb, nullptr, out);
   count_launch(2);
   return cudaGetLastError();
 }
@@ -341,7 +357,7 @@ template <typename T>
 cudaError_t launch_bicg_p(void* p, const void* r, const void* v, const double2* beta,
                           const double2* omega, long long N, int R, cudaStream_t s) {
   using C = typename CT<T>::type;
-  bicg_p_k<T><<<grid_for(N, R), kThreads, 0, s>>>((C*)p, (const C*)r, (const C*)v, beta, omega, N);
+  (void)launch_k(bicg_p_k<T>, grid_for(N, R), kThreads, 0, s, (C*)p, (const C*)r, (const C*)v, beta, omega, N);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -350,7 +366,7 @@ template <typename T>
 cudaError_t launch_bicg_s(void* sv, const void* r, const void* v, const double2* alpha, long long N,
                           int R, cudaStream_t s) {
   using C = typename CT<T>::type;
-  bicg_s_k<T><<<grid_for(N, R), kThreads, 0, s>>>((C*)sv, (const C*)r, (const C*)v, alpha, N);
+  (void)launch_k(bicg_s_k<T>, grid_for(N, R), kThreads, 0, s, (C*)sv, (const C*)r, (const C*)v, alpha, N);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -360,7 +376,7 @@ cudaError_t launch_bicg_xr(void* x, void* r, const void* sv, const void* phat, c
                            const void* t, const double2* alpha, const double2* omega, long long N,
                            int R, cudaStream_t s) {
   using C = typename CT<T>::type;
-  bicg_xr_k<T><<<grid_for(N, R), kThreads, 0, s>>>((C*)x, (C*)r, (const C*)sv, (const C*)phat,
+  (void)launch_k(bicg_xr_k<T>, grid_for(N, R), kThreads, 0, s, (C*)x, (C*)r, (const C*)sv, (const C*)phat,
                                                    (const C*)shat, (const C*)t, alpha, omega, N);
   count_launch(1);
   return cudaGetLastError();
@@ -371,7 +387,7 @@ cudaError_t launch_restrict(const void* fine, const int nf[3], void* coarse, con
                             cudaStream_t s) {
   using C = typename CT<T>::type;
   const long long Nc = (long long)nc[0] * nc[1] * nc[2];
-  restrict_k<T><<<grid_for(Nc, R, 1), kThreads, 0, s>>>((const C*)fine, nf[0], nf[1], nf[2], (C*)coarse,
+  (void)launch_k(restrict_k<T>, grid_for(Nc, R, 1), kThreads, 0, s, (const C*)fine, nf[0], nf[1], nf[2], (C*)coarse,
                                                         nc[0], nc[1], nc[2]);
   count_launch(1);
   return cudaGetLastError();
@@ -382,7 +398,7 @@ cudaError_t launch_prolong_add(void* fine, const int nf[3], const void* coarse, 
                                cudaStream_t s) {
   using C = typename CT<T>::type;
   const long long Nf = (long long)nf[0] * nf[1] * nf[2];
-  prolong_k<T><<<grid_for(Nf, R, 1), kThreads, 0, s>>>((C*)fine, nf[0], nf[1], nf[2], (const C*)coarse,
+  (void)launch_k(prolong_k<T>, grid_for(Nf, R, 1), kThreads, 0, s, (C*)fine, nf[0], nf[1], nf[2], (const C*)coarse,
                                                        nc[0], nc[1], nc[2]);
   count_launch(1);
   return cudaGetLastError();
@@ -391,28 +407,28 @@ cudaError_t launch_prolong_add(void* fine, const int nf[3], const void* coarse, 
 cudaError_t launch_inject_velocity(const float* vf, const int nf[3], float* vc, const int nc[3],
                                    cudaStream_t s) {
   const long long Nc = (long long)nc[0] * nc[1] * nc[2];
-  inject_v_k<<<grid_for(Nc, 1, 1), kThreads, 0, s>>>(vf, nf[0], nf[1], vc, nc[0], nc[1], nc[2]);
+  (void)launch_k(inject_v_k, grid_for(Nc, 1, 1), kThreads, 0, s, vf, nf[0], nf[1], vc, nc[0], nc[1], nc[2]);
   count_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cast_scale(const double2* r64, float2* r32, const double* scale, long long N, int R,
                               cudaStream_t s) {
-  cast_scale_k<<<grid_for(N, R), kThreads, 0, s>>>(r64, r32, scale, N);
+  (void)launch_k(cast_scale_k, grid_for(N, R), kThreads, 0, s, r64, r32, scale, N);
   count_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_mixed(double2* x64, const float2* d32, const double* scale, long long N, int R,
                               cudaStream_t s) {
-  axpy_mixed_k<float2><<<grid_for(N, R), kThreads, 0, s>>>(x64, d32, scale, N);
+  (void)launch_k(axpy_mixed_k<float2>, grid_for(N, R), kThreads, 0, s, x64, d32, scale, N);
   count_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_c128(double2* x64, const double2* d64, const double* scale, long long N, int R,
                              cudaStream_t s) {
-  axpy_mixed_k<double2><<<grid_for(N, R), kThreads, 0, s>>>(x64, d64, scale, N);
+  (void)launch_k(axpy_mixed_k<double2>, grid_for(N, R), kThreads, 0, s, x64, d64, scale, N);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -426,26 +442,26 @@ template <typename T>
 cudaError_t launch_add_sources(void* r, long long N, const SourceEntry* e, int n, cudaStream_t s) {
   using C = typename CT<T>::type;
   if (n <= 0) return cudaSuccess;
-  add_sources_k<T><<<(n + 127) / 128, 128, 0, s>>>((C*)r, N, e, n);
+  (void)launch_k(add_sources_k<T>, (n + 127) / 128, 128, 0, s, (C*)r, N, e, n);
   count_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scal_beta(double2* beta, double2* rho, const double2* rho_new, const double2* alpha,
                              const double2* omega, const int* active, int* brk, int R, cudaStream_t s) {
-  scal_beta_k<<<(R + 127) / 128, 128, 0, s>>>(beta, rho, rho_new, alpha, omega, active, brk, R);
+  (void)launch_k(scal_beta_k, (R + 127) / 128, 128, 0, s, beta, rho, rho_new, alpha, omega, active, brk, R);
   count_launch(1);
   return cudaGetLastError();
 }
 cudaError_t launch_scal_alpha(double2* alpha, const double2* rho, const double2* rv, int* active,
                               int* brk, int R, cudaStream_t s) {
-  scal_alpha_k<<<(R + 127) / 128, 128, 0, s>>>(alpha, rho, rv, active, brk, R);
+  (void)launch_k(scal_alpha_k, (R + 127) / 128, 128, 0, s, alpha, rho, rv, active, brk, R);
   count_launch(1);
   return cudaGetLastError();
 }
 cudaError_t launch_scal_omega(double2* omega, const double2* ts, const double* tt, int* active,
                               int* brk, int R, cudaStream_t s) {
-  scal_omega_k<<<(R + 127) / 128, 128, 0, s>>>(omega, ts, tt, active, brk, R);
+  (void)launch_k(scal_omega_k, (R + 127) / 128, 128, 0, s, omega, ts, tt, active, brk, R);
   count_launch(1);
   return cudaGetLastError();
 }

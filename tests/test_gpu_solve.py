@@ -188,3 +188,37 @@ def test_autotune_option_records_a_configuration(ctx):
         assert rep["status"] == 0
         outs.append(out)
     assert torch.linalg.vector_norm(outs[0] - outs[1]) <= 1e-6 * torch.linalg.vector_norm(outs[0])
+
+
+_PDL_CHILD = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[2])
+from oracle import weights as W
+from paper_2108_08730_gb300 import binding as B, synth
+wl = synth.homogeneous(n=28, npml=5)
+wl.v = synth.random_velocity(wl.shape, 41, 1500.0, 2400.0)
+wl.v_ref = 2400.0
+ctx = B.Context(0, table=W.fit_table()[1])
+out = torch.zeros((2,) + wl.shape, dtype=torch.complex128, device="cuda")
+src = [(14, 13, 12, 0, 1.0), (9, 17, 15, 1, 1j)]
+rep = ctx.solve(B.grid_of(wl), torch.from_numpy(wl.v).cuda(), src, 2, out, check=False)
+assert rep["status"] == 0, rep
+np.save(sys.argv[1], out.cpu().numpy())
+"""
+
+
+def test_dependent_launch_does_not_change_results(tmp_path):
+    # Every solver kernel is launched with programmatic dependent launch
+    # (HX_PDL, default on) and waits for its predecessor before touching
+    # memory; the wavefield must be bit-identical with the attribute off.
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = {}
+    for flag in ("0", "1"):
+        f = tmp_path / f"pdl{flag}.npy"
+        env = dict(os.environ, HX_PDL=flag)
+        subprocess.run([sys.executable, "-c", _PDL_CHILD, str(f), root], env=env, check=True, timeout=600)
+        res[flag] = np.load(f)
+    assert np.array_equal(res["0"], res["1"])
