@@ -78,6 +78,8 @@ struct SolverImpl : Solver {
   double2 *rho, *rho_new, *alpha, *omega, *beta, *rv, *ts;
   double *tt, *rn2, *bn2, *scale;
   int *active, *brk;
+  unsigned* count;                      // arrival counters of the reductions
+  BicgScalars scalars() const { return BicgScalars{rho, rho_new, alpha, omega, beta, rv, ts, tt, rn2, active, brk, count}; }
   // pinned host mirrors read at convergence checks
   double* pin_rn2 = nullptr;
   int* pin_act = nullptr;
@@ -251,33 +253,33 @@ class Run {
     return cur == e ? HX_OK : fail(ctx, HX_ERR_STATE, "V-cycle buffer parity");
   }
 
-  // One BiCGStab iteration (all RHS), launches only.
+  // One BiCGStab iteration (all RHS), launches only.  On entry rho_new and
+  // beta of this iteration are already on the device (the previous
+  // iteration's last kernel, or the reduction before the first iteration).
   template <typename T>
   int bicg_iteration(const OpDesc<T>& A) {
     const int R = S->R;
     const long long N = S->N[0];
     double2* part = (double2*)S->part.p;
-    HX_CK(launch_dot<T>(S->rhat.p, S->r.p, N, R, part, S->rho_new, stream));
-    HX_CK(launch_scal_beta(S->beta, S->rho, S->rho_new, S->alpha, S->omega, S->active, S->brk, R, stream));
+    const BicgScalars sc = S->scalars();
     HX_CK(launch_bicg_p<T>(S->p.p, S->r.p, S->v.p, S->beta, S->omega, N, R, stream));
     int st = vcycle<T>(0, S->p.p, S->ph.p, S->tmp.p);
     if (st) return st;
     HX_CK(stencil<T>(0, A, kApply, S->ph.p, nullptr, S->v.p, 0.0));
-    HX_CK(launch_dot<T>(S->rhat.p, S->v.p, N, R, part, S->rv, stream));
-    HX_CK(launch_scal_alpha(S->alpha, S->rho, S->rv, S->active, S->brk, R, stream));
+    HX_CK(launch_bicg_reduce<T>(kRedAlpha, S->rhat.p, S->v.p, N, R, part, sc, stream));
     HX_CK(launch_bicg_s<T>(S->s.p, S->r.p, S->v.p, S->alpha, N, R, stream));
     st = vcycle<T>(0, S->s.p, S->sh.p, S->tmp.p);
     if (st) return st;
     HX_CK(stencil<T>(0, A, kApply, S->sh.p, nullptr, S->t.p, 0.0));
-    HX_CK(launch_dot<T>(S->t.p, S->s.p, N, R, part, S->ts, stream));
-    HX_CK(launch_norm2<T>(S->t.p, N, R, part, S->tt, stream));
-    HX_CK(launch_scal_omega(S->omega, S->ts, S->tt, S->active, S->brk, R, stream));
-    HX_CK(launch_bicg_xr<T>(S->x.p, S->r.p, S->s.p, S->ph.p, S->sh.p, S->t.p, S->alpha, S->omega, N, R, stream));
+    HX_CK(launch_bicg_reduce<T>(kRedOmega, S->t.p, S->s.p, N, R, part, sc, stream));
+    HX_CK(launch_bicg_xr_reduce<T>(S->x.p, S->r.p, S->s.p, S->ph.p, S->sh.p, S->t.p, S->rhat.p, N, R, part, sc,
+                                   stream));
     return HX_OK;
   }
 
-  // k iterations followed by the residual norms and active flags copied to
-  // pinned host memory: the unit replayed between host convergence checks.
+  // k iterations followed by the residual norms (left by the last iteration)
+  // and active flags copied to pinned host memory: the unit replayed between
+  // host convergence checks.
   template <typename T>
   int bicg_block(const OpDesc<T>& A, int k) {
     for (int j = 0; j < k; ++j) {
@@ -285,7 +287,6 @@ class Run {
       if (st) return st;
     }
     const int R = S->R;
-    HX_CK(launch_norm2<T>(S->r.p, S->N[0], R, (double2*)S->part.p, S->rn2, stream));
     HX_CK(cudaMemcpyAsync(S->pin_rn2, S->rn2, R * sizeof(double), cudaMemcpyDeviceToHost, stream));
     HX_CK(cudaMemcpyAsync(S->pin_act, S->active, R * sizeof(int), cudaMemcpyDeviceToHost, stream));
     return HX_OK;
@@ -386,6 +387,8 @@ class Run {
     for (int k = 0; k < R; ++k)
       if (!(S->h_bn2[k] > 0)) S->h_active[k] = 0;
     HX_CK(cudaMemcpyAsync(S->active, S->h_active.data(), R * sizeof(int), cudaMemcpyHostToDevice, stream));
+    // rho_new = (rhat, r) and the first beta step (p = r whatever beta is, since p = v = 0)
+    HX_CK(launch_bicg_reduce<T>(kRedBeta, rhat, r, N, R, (double2*)S->part.p, S->scalars(), stream));
     (void)p; (void)v; (void)sv; (void)t; (void)ph; (void)sh; (void)tmp;
     int it = 0;
     bool any = false;
@@ -717,8 +720,8 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
         if (e == cudaSuccess) e = S->me[l].alloc(lb);
         if (e == cudaSuccess) e = S->mw[l].alloc(lb);
       }
-      if (e == cudaSuccess) e = S->sc.alloc((size_t)nrhs * (7 * 16 + 4 * 8 + 2 * 4) + 64);
-      if (e == cudaSuccess) e = S->part.alloc((size_t)nrhs * reduce_blocks(S->N[0]) * 16);
+      if (e == cudaSuccess) e = S->sc.alloc((size_t)nrhs * (7 * 16 + 4 * 8 + 3 * 4) + 64);
+      if (e == cudaSuccess) e = S->part.alloc((size_t)2 * nrhs * reduce_blocks(S->N[0]) * 16);
       if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "solver workspace"));
       char* q = (char*)S->sc.p;
       auto take = [&](size_t bytes) { char* r = q; q += bytes; return r; };
@@ -735,6 +738,9 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       S->scale = (double*)take(nrhs * 8);
       S->active = (int*)take(nrhs * 4);
       S->brk = (int*)take(nrhs * 4);
+      S->count = (unsigned*)take(nrhs * 4);
+      e = cudaMemsetAsync(S->count, 0, nrhs * 4, stream);
+      if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "solver workspace"));
       S->h_rn2.resize(nrhs);
       if (cudaHostAlloc(&S->pin_rn2, nrhs * sizeof(double), cudaHostAllocDefault) != cudaSuccess ||
           cudaHostAlloc(&S->pin_act, nrhs * sizeof(int), cudaHostAllocDefault) != cudaSuccess ||

@@ -117,26 +117,6 @@ __global__ void bicg_s_k(typename CT<T>::type* __restrict__ sv, const typename C
     sv[o + i] = cfma(mal, v[o + i], r[o + i]);
 }
 
-template <typename T>
-__global__ void bicg_xr_k(typename CT<T>::type* __restrict__ x, typename CT<T>::type* __restrict__ r,
-                          const typename CT<T>::type* __restrict__ sv,
-                          const typename CT<T>::type* __restrict__ ph,
-                          const typename CT<T>::type* __restrict__ sh,
-                          const typename CT<T>::type* __restrict__ t, const double2* alpha,
-                          const double2* omega, long long N) {
-  pdl_enter();
-  using C = typename CT<T>::type;
-  const int k = blockIdx.y;
-  const C al = from_d2<C>(alpha[k]), om = from_d2<C>(omega[k]);
-  const C mom = cmk(-om.x, -om.y);
-  const long long o = (long long)k * N;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
-    x[o + i] = cfma(om, sh[o + i], cfma(al, ph[o + i], x[o + i]));
-    r[o + i] = cfma(mom, t[o + i], sv[o + i]);
-  }
-}
-
 // full weighting: coarse node I <- fine nodes 2I + s, s in {-1,0,1}^3, weight
 // prod_d (1/2)^{|s_d|} / 8; fine nodes outside the grid are zero.
 template <typename T>
@@ -261,35 +241,129 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ bool tiny(double2 a) { return !(a.x * a.x + a.y * a.y > 1e-300); }
 
-__global__ void scal_beta_k(double2* beta, double2* rho, const double2* rho_new, const double2* alpha,
-                            const double2* omega, const int* active, int* brk, int R) {
-  pdl_enter();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  if (!active[r]) { beta[r] = make_double2(0, 0); return; }
-  if (tiny(rho[r]) || tiny(omega[r])) { beta[r] = make_double2(0, 0); brk[r] = 1; return; }
-  beta[r] = cdiv(cmul(rho_new[r], alpha[r]), cmul(rho[r], omega[r]));
-  rho[r] = rho_new[r];
+// Per-RHS scalar steps of BiCGStab (thread 0 of the last block of RHS r).
+__device__ void beta_step(const BicgScalars& sc, int r) {
+  if (!sc.active[r]) { sc.beta[r] = make_double2(0, 0); return; }
+  if (tiny(sc.rho[r]) || tiny(sc.omega[r])) { sc.beta[r] = make_double2(0, 0); sc.brk[r] = 1; return; }
+  sc.beta[r] = cdiv(cmul(sc.rho_new[r], sc.alpha[r]), cmul(sc.rho[r], sc.omega[r]));
+  sc.rho[r] = sc.rho_new[r];
 }
 
-__global__ void scal_alpha_k(double2* alpha, const double2* rho, const double2* rv, int* active,
-                             int* brk, int R) {
-  pdl_enter();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  if (!active[r]) { alpha[r] = make_double2(0, 0); return; }
-  if (tiny(rv[r])) { alpha[r] = make_double2(0, 0); active[r] = 0; brk[r] = 1; return; }
-  alpha[r] = cdiv(rho[r], rv[r]);
+__device__ void alpha_step(const BicgScalars& sc, int r) {
+  if (!sc.active[r]) { sc.alpha[r] = make_double2(0, 0); return; }
+  if (tiny(sc.rv[r])) { sc.alpha[r] = make_double2(0, 0); sc.active[r] = 0; sc.brk[r] = 1; return; }
+  sc.alpha[r] = cdiv(sc.rho[r], sc.rv[r]);
 }
 
-__global__ void scal_omega_k(double2* omega, const double2* ts, const double* tt, int* active,
-                             int* brk, int R) {
+__device__ void omega_step(const BicgScalars& sc, int r) {
+  if (!sc.active[r]) { sc.omega[r] = make_double2(0, 0); return; }
+  if (!(sc.tt[r] > 1e-300)) { sc.omega[r] = make_double2(0, 0); sc.active[r] = 0; sc.brk[r] = 1; return; }
+  sc.omega[r] = make_double2(sc.ts[r].x / sc.tt[r], sc.ts[r].y / sc.tt[r]);
+}
+
+// sum of nblk partials in block order (the same order as dot_finish)
+__device__ double2 partials_sum(const double2* p, int nblk) {
+  double2 s = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < nblk; i += kThreads) {
+    const double2 v = __ldcg(p + i);
+    s.x += v.x;
+    s.y += v.y;
+  }
+  return block_sum(s);
+}
+
+// The end of a one-launch reduction: block b's sums t (and q) become
+// partials; the last block of RHS r to arrive adds the partials in block
+// order, stores the result and takes the scalar step.  Call with the block's
+// sums in thread 0 (block_sum), from every thread of the block.
+template <int KIND>
+__device__ void reduce_tail(double2 t, double2 q, double2* part, const BicgScalars& sc) {
+  constexpr bool TWO = KIND == kRedOmega || KIND == kRedBetaNorm;
+  const int r = blockIdx.y, nb = gridDim.x;
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    part[(long long)r * nb + blockIdx.x] = t;
+    if (TWO) part[(long long)(gridDim.y + r) * nb + blockIdx.x] = q;
+    __threadfence();                                   // partials visible before the arrival
+    s_last = atomicAdd(sc.count + r, 1u) == (unsigned)(nb - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const double2 f = partials_sum(part + (long long)r * nb, nb);
+  double2 g = make_double2(0.0, 0.0);
+  if (TWO) g = partials_sum(part + (long long)(gridDim.y + r) * nb, nb);
+  if (threadIdx.x == 0) {
+    sc.count[r] = 0;
+    if (KIND == kRedBeta || KIND == kRedBetaNorm) { sc.rho_new[r] = f; beta_step(sc, r); }
+    if (KIND == kRedAlpha) { sc.rv[r] = f; alpha_step(sc, r); }
+    if (KIND == kRedOmega) { sc.ts[r] = f; sc.tt[r] = g.x; omega_step(sc, r); }
+    if (KIND == kRedNorm) sc.rn2[r] = f.x;
+    if (KIND == kRedBetaNorm) sc.rn2[r] = g.x;
+  }
+}
+
+// One-launch reduction + scalar step (see launch_bicg_reduce).  The per-thread
+// and per-block arithmetic is that of dot_partial / dot_finish.
+template <typename T, int KIND>
+__global__ void __launch_bounds__(kThreads)
+bicg_reduce_k(const typename CT<T>::type* __restrict__ a, const typename CT<T>::type* __restrict__ b,
+              long long N, double2* __restrict__ part, BicgScalars sc) {
   pdl_enter();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
-  if (!active[r]) { omega[r] = make_double2(0, 0); return; }
-  if (!(tt[r] > 1e-300)) { omega[r] = make_double2(0, 0); active[r] = 0; brk[r] = 1; return; }
-  omega[r] = make_double2(ts[r].x / tt[r], ts[r].y / tt[r]);
+  using C = typename CT<T>::type;
+  const int r = blockIdx.y;
+  const C* ar = a + (long long)r * N;
+  const C* br = b + (long long)r * N;
+  T sx = 0, sy = 0, qx = 0;
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < N;
+       i += (long long)gridDim.x * kThreads) {
+    const C u = ar[i];
+    if (KIND == kRedNorm) {
+      sx = fma(u.x, u.x, fma(u.y, u.y, sx));
+    } else {
+      const C w = br[i];
+      sx = fma(u.x, w.x, fma(u.y, w.y, sx));     // Re(conj(u) w)
+      sy = fma(u.x, w.y, fma(-u.y, w.x, sy));    // Im(conj(u) w)
+      if (KIND == kRedOmega) qx = fma(u.x, u.x, fma(u.y, u.y, qx));
+    }
+  }
+  const double2 t = block_sum(make_double2((double)sx, (double)sy));
+  double2 q = make_double2(0.0, 0.0);
+  if (KIND == kRedOmega) q = block_sum(make_double2((double)qx, 0.0));
+  reduce_tail<KIND>(t, q, part, sc);
+}
+
+// x += alpha phat + omega shat;  r = s - omega t;  then the kRedBetaNorm
+// reduction of the new r: rho_new = (rhat, r), the beta step of the next
+// iteration, rn2 = |r|^2.  Same block partition as bicg_reduce_k, so the
+// sums are those of the separate reductions.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+bicg_xr_reduce_k(typename CT<T>::type* __restrict__ x, typename CT<T>::type* __restrict__ r,
+                 const typename CT<T>::type* __restrict__ sv, const typename CT<T>::type* __restrict__ ph,
+                 const typename CT<T>::type* __restrict__ sh, const typename CT<T>::type* __restrict__ t,
+                 const typename CT<T>::type* __restrict__ rhat, long long N, double2* __restrict__ part,
+                 BicgScalars sc) {
+  pdl_enter();
+  using C = typename CT<T>::type;
+  const int k = blockIdx.y;
+  const C al = from_d2<C>(sc.alpha[k]), om = from_d2<C>(sc.omega[k]);
+  const C mom = cmk(-om.x, -om.y);
+  const long long o = (long long)k * N;
+  T sx = 0, sy = 0, qx = 0;
+  for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < N;
+       i += (long long)gridDim.x * kThreads) {
+    x[o + i] = cfma(om, sh[o + i], cfma(al, ph[o + i], x[o + i]));
+    const C w = cfma(mom, t[o + i], sv[o + i]);
+    r[o + i] = w;
+    const C u = rhat[o + i];
+    sx = fma(u.x, w.x, fma(u.y, w.y, sx));
+    sy = fma(u.x, w.y, fma(-u.y, w.x, sy));
+    qx = fma(w.x, w.x, fma(w.y, w.y, qx));
+  }
+  const double2 tt = block_sum(make_double2((double)sx, (double)sy));
+  const double2 q = block_sum(make_double2((double)qx, 0.0));
+  reduce_tail<kRedBetaNorm>(tt, q, part, sc);
 }
 
 template <typename T>
@@ -333,17 +407,6 @@ int reduce_blocks(long long N) {
 }
 
 template <typename T>
-cudaError_t launch_dot(const void* a, const void* b, long long N, int R, double2* part, double2* out,
-                       cudaStream_t s) {
-  using C = typename CT<T>::type;
-  const int nb = reduce_blocks(N);
-  (void)launch_k(dot_partial<T, false>, dim3(nb, R), kThreads, 0, s, (const C*)a, (const C*)b, N, part);
-  (void)launch_k(dot_finish, R, kThreads, 0, s, part, nb, out, nullptr);
-  count_launch(2);
-  return cudaGetLastError();
-}
-
-template <typename T>
 cudaError_t launch_norm2(const void* a, long long N, int R, double2* part, double* out, cudaStream_t s) {
   using C = typename CT<T>::type;
   const int nb = reduce_blocks(N);
@@ -367,17 +430,6 @@ cudaError_t launch_bicg_s(void* sv, const void* r, const void* v, const double2*
                           int R, cudaStream_t s) {
   using C = typename CT<T>::type;
   (void)launch_k(bicg_s_k<T>, grid_for(N, R), kThreads, 0, s, (C*)sv, (const C*)r, (const C*)v, alpha, N);
-  count_launch(1);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_bicg_xr(void* x, void* r, const void* sv, const void* phat, const void* shat,
-                           const void* t, const double2* alpha, const double2* omega, long long N,
-                           int R, cudaStream_t s) {
-  using C = typename CT<T>::type;
-  (void)launch_k(bicg_xr_k<T>, grid_for(N, R), kThreads, 0, s, (C*)x, (C*)r, (const C*)sv, (const C*)phat,
-                                                   (const C*)shat, (const C*)t, alpha, omega, N);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -447,37 +499,46 @@ cudaError_t launch_add_sources(void* r, long long N, const SourceEntry* e, int n
   return cudaGetLastError();
 }
 
-cudaError_t launch_scal_beta(double2* beta, double2* rho, const double2* rho_new, const double2* alpha,
-                             const double2* omega, const int* active, int* brk, int R, cudaStream_t s) {
-  (void)launch_k(scal_beta_k, (R + 127) / 128, 128, 0, s, beta, rho, rho_new, alpha, omega, active, brk, R);
+template <typename T>
+cudaError_t launch_bicg_reduce(int kind, const void* a, const void* b, long long N, int R, double2* part,
+                               const BicgScalars& sc, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  const dim3 g(reduce_blocks(N), R);
+  const C *ca = (const C*)a, *cb = (const C*)(b ? b : a);
+  switch (kind) {
+    case kRedBeta: (void)launch_k(bicg_reduce_k<T, kRedBeta>, g, kThreads, 0, s, ca, cb, N, part, sc); break;
+    case kRedAlpha: (void)launch_k(bicg_reduce_k<T, kRedAlpha>, g, kThreads, 0, s, ca, cb, N, part, sc); break;
+    case kRedOmega: (void)launch_k(bicg_reduce_k<T, kRedOmega>, g, kThreads, 0, s, ca, cb, N, part, sc); break;
+    case kRedNorm: (void)launch_k(bicg_reduce_k<T, kRedNorm>, g, kThreads, 0, s, ca, cb, N, part, sc); break;
+    default: return cudaErrorInvalidValue;
+  }
   count_launch(1);
   return cudaGetLastError();
 }
-cudaError_t launch_scal_alpha(double2* alpha, const double2* rho, const double2* rv, int* active,
-                              int* brk, int R, cudaStream_t s) {
-  (void)launch_k(scal_alpha_k, (R + 127) / 128, 128, 0, s, alpha, rho, rv, active, brk, R);
-  count_launch(1);
-  return cudaGetLastError();
-}
-cudaError_t launch_scal_omega(double2* omega, const double2* ts, const double* tt, int* active,
-                              int* brk, int R, cudaStream_t s) {
-  (void)launch_k(scal_omega_k, (R + 127) / 128, 128, 0, s, omega, ts, tt, active, brk, R);
+
+template <typename T>
+cudaError_t launch_bicg_xr_reduce(void* x, void* r, const void* sv, const void* phat, const void* shat,
+                                  const void* t, const void* rhat, long long N, int R, double2* part,
+                                  const BicgScalars& sc, cudaStream_t s) {
+  using C = typename CT<T>::type;
+  (void)launch_k(bicg_xr_reduce_k<T>, dim3(reduce_blocks(N), R), kThreads, 0, s, (C*)x, (C*)r, (const C*)sv,
+                 (const C*)phat, (const C*)shat, (const C*)t, (const C*)rhat, N, part, sc);
   count_launch(1);
   return cudaGetLastError();
 }
 
 #define HX_INST(T)                                                                                  \
-  template cudaError_t launch_dot<T>(const void*, const void*, long long, int, double2*, double2*, \
-                                     cudaStream_t);                                                \
+  template cudaError_t launch_bicg_reduce<T>(int, const void*, const void*, long long, int, double2*, \
+                                             const BicgScalars&, cudaStream_t);                   \
+  template cudaError_t launch_bicg_xr_reduce<T>(void*, void*, const void*, const void*, const void*, \
+                                                const void*, const void*, long long, int, double2*, \
+                                                const BicgScalars&, cudaStream_t);                \
   template cudaError_t launch_norm2<T>(const void*, long long, int, double2*, double*,             \
                                        cudaStream_t);                                              \
   template cudaError_t launch_bicg_p<T>(void*, const void*, const void*, const double2*,           \
                                         const double2*, long long, int, cudaStream_t);             \
   template cudaError_t launch_bicg_s<T>(void*, const void*, const void*, const double2*,           \
                                         long long, int, cudaStream_t);                             \
-  template cudaError_t launch_bicg_xr<T>(void*, void*, const void*, const void*, const void*,      \
-                                         const void*, const double2*, const double2*, long long,   \
-                                         int, cudaStream_t);                                       \
   template cudaError_t launch_restrict<T>(const void*, const int*, void*, const int*, int,         \
                                           cudaStream_t);                                           \
   template cudaError_t launch_prolong_add<T>(void*, const int*, const void*, const int*, int,      \

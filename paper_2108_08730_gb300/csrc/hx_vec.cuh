@@ -13,11 +13,7 @@ namespace hx {
 // Deterministic reductions: every RHS is reduced over the same fixed blocks in
 // the same order, so a result does not depend on how many RHS share the batch.
 int reduce_blocks(long long N);
-// out[r] = sum_i conj(a[r,i]) b[r,i]   (partials: >= R * reduce_blocks(N) double2)
-template <typename T>
-cudaError_t launch_dot(const void* a, const void* b, long long N, int R, double2* partials,
-                       double2* out, cudaStream_t s);
-// out[r] = sum_i |a[r,i]|^2
+// out[r] = sum_i |a[r,i]|^2   (partials: >= R * reduce_blocks(N) double2)
 template <typename T>
 cudaError_t launch_norm2(const void* a, long long N, int R, double2* partials, double* out,
                          cudaStream_t s);
@@ -29,11 +25,6 @@ cudaError_t launch_bicg_p(void* p, const void* r, const void* v, const double2* 
 template <typename T>
 cudaError_t launch_bicg_s(void* sv, const void* r, const void* v, const double2* alpha, long long N,
                           int R, cudaStream_t s);
-template <typename T>
-cudaError_t launch_bicg_xr(void* x, void* r, const void* sv, const void* phat, const void* shat,
-                           const void* t, const double2* alpha, const double2* omega, long long N,
-                           int R, cudaStream_t s);
-
 // Multigrid transfers between a fine level (nf) and its coarse level (nc):
 // coarse = full weighting of fine;  fine += trilinear(coarse).
 template <typename T>
@@ -66,20 +57,39 @@ struct SourceEntry {
 template <typename T>
 cudaError_t launch_add_sources(void* r, long long N, const SourceEntry* e, int n, cudaStream_t s);
 
-// Per-RHS scalar steps of BiCGStab (one thread per RHS).
-//   beta step : beta = (rho_new / rho) (alpha / omega); rho = rho_new
-//   alpha step: alpha = rho / rv        (rv = (rhat, v))
-//   omega step: omega = ts / tt         (ts = (t, s), tt = |t|^2)
-// Inactive RHS (active[r] == 0) get zero alpha/omega/beta, so the vector
-// updates leave them unchanged.  A zero denominator deactivates the RHS and
-// sets breakdown[r] = 1.
-cudaError_t launch_scal_beta(double2* beta, double2* rho, const double2* rho_new,
-                             const double2* alpha, const double2* omega, const int* active,
-                             int* breakdown, int R, cudaStream_t s);
-cudaError_t launch_scal_alpha(double2* alpha, const double2* rho, const double2* rv, int* active,
-                              int* breakdown, int R, cudaStream_t s);
-cudaError_t launch_scal_omega(double2* omega, const double2* ts, const double* tt, int* active,
-                              int* breakdown, int R, cudaStream_t s);
+// Per-RHS scalars of BiCGStab on the device (arrays of length R) and the
+// reductions that produce them.  Each reduction is one launch: every block
+// writes its partial sum, and the last block of each RHS to arrive (a
+// per-RHS arrival counter) adds the partials in block order, stores the sum
+// and takes the scalar step, then resets the counter.  The block partition and
+// both summation orders are fixed, so the result does not depend on timing or
+// on how many RHS share the batch.
+//   kRedBeta : rho_new = (rhat, r);  beta = (rho_new / rho)(alpha / omega), rho = rho_new
+//   kRedAlpha: rv = (rhat, v);       alpha = rho / rv
+//   kRedOmega: ts = (t, s), tt = |t|^2 (one pass over t);  omega = ts / tt
+//   kRedNorm : rn2 = |a|^2
+//   kRedBetaNorm (launch_bicg_xr_reduce only): kRedBeta of the updated r, and rn2 = |r|^2
+// (x, y) = sum_i conj(x_i) y_i.  Inactive RHS (active[r] == 0) get zero
+// alpha / omega / beta, so the vector updates leave them unchanged; a zero
+// denominator deactivates the RHS and sets brk[r] = 1.
+struct BicgScalars {
+  double2 *rho, *rho_new, *alpha, *omega, *beta, *rv, *ts;
+  double *tt, *rn2;
+  int *active, *brk;
+  unsigned* count;   // R arrival counters, zero between launches
+};
+enum { kRedBeta = 0, kRedAlpha = 1, kRedOmega = 2, kRedNorm = 3, kRedBetaNorm = 4 };
+// partials: >= 2 * R * reduce_blocks(N) double2; b is unused for kRedNorm
+template <typename T>
+cudaError_t launch_bicg_reduce(int kind, const void* a, const void* b, long long N, int R, double2* partials,
+                               const BicgScalars& sc, cudaStream_t s);
+// The last update of a BiCGStab iteration fused with the next iteration's
+// first reduction: x += alpha phat + omega shat, r = s - omega t, then
+// kRedBetaNorm over the new r (with rhat).
+template <typename T>
+cudaError_t launch_bicg_xr_reduce(void* x, void* r, const void* sv, const void* phat, const void* shat,
+                                  const void* t, const void* rhat, long long N, int R, double2* partials,
+                                  const BicgScalars& sc, cudaStream_t s);
 
 }  // namespace hx
 
