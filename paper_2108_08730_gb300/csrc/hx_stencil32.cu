@@ -260,6 +260,10 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
   float v1[YB];                                        // v at plane z + 1 (PREFETCH) or z
   const float* vp[YB];                                 // v at the plane after v1's
   long long yo[YB];                                    // element offset of (ix, iy, z) in field r0
+  // b of a single RHS is fetched one plane ahead, so its latency is not
+  // exposed after the per-plane barrier (Jacobi and residual sweeps)
+  constexpr bool BPF = MODE != kApply && RB == 1;
+  float2 bnx[YB];                                      // b at plane z (BPF)
 #pragma unroll
   for (int j = 0; j < YB; ++j) {
     const int iy = iyb + j;
@@ -277,6 +281,7 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
       vp[j] = op.v + o + plane;
     }
     yo[j] = o + (long long)r0 * rstride;
+    bnx[j] = BPF && b && act[j] && z0 < z1 ? b[yo[j]] : make_float2(0.f, 0.f);
   }
 
   auto step = [&](auto ptag, int z) {
@@ -301,6 +306,11 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
       vp[j] += plane;
       const long long off = yo[j];
       yo[j] += plane;
+      float2 bcur = make_float2(0.f, 0.f);
+      if (BPF) {
+        bcur = bnx[j];
+        if (b && act[j] && z + 1 < z1) bnx[j] = b[off + plane];
+      }
       if (!act[j]) continue;
       const float tf = t.tf, m = t.m;
       const float* tq = op.tab + t.i0 * kTabW;
@@ -358,8 +368,8 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
           if (r == 0 || r < rcount) {
             const long long o = off + (r == 0 ? 0 : r * rstride);
             float2 res = acc;
-            if (MODE == kResidual) res = b ? psub(b[o], acc) : make_float2(-acc.x, -acc.y);
-            if (MODE == kJacobi) res = cfmac(dinv, psub(b[o], acc), c0);
+            if (MODE == kResidual) res = b ? psub(BPF ? bcur : b[o], acc) : make_float2(-acc.x, -acc.y);
+            if (MODE == kJacobi) res = cfmac(dinv, psub(BPF ? bcur : b[o], acc), c0);
             y[o] = res;
           }
         }
@@ -416,14 +426,14 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
                       cfmac(make_float2(-(az.x + az.z), -(az.y + az.w)), Fz[1], acc)));
           const long long o = off + r * rstride;
           float2 res = acc;
-          if (MODE == kResidual) res = b ? psub(b[o], acc) : make_float2(-acc.x, -acc.y);
+          if (MODE == kResidual) res = b ? psub(BPF ? bcur : b[o], acc) : make_float2(-acc.x, -acc.y);
           if (MODE == kJacobi) {
             const float sdx = ax.x + ax.z + ay.x + ay.z + az.x + az.z;
             const float sdy = ax.y + ax.w + ay.y + ay.w + az.y + az.w;
             const float2 diag = make_float2(fmaf(mc.x, m01.x, -t0 * sdx), fmaf(mc.y, m01.x, -t0 * sdy));
             float2 dinv = crcpf(diag);
             dinv = make_float2(omega_j * dinv.x, omega_j * dinv.y);
-            res = cfmac(dinv, psub(b[o], acc), xc);
+            res = cfmac(dinv, psub(BPF ? bcur : b[o], acc), xc);
           }
           y[o] = res;
         }
