@@ -35,7 +35,21 @@ For the complex-shifted Laplacian used by the GPU preconditioner omega^2 is
 replaced by (1 + i beta) omega^2 (beta = 0 is the paper's operator).
 
 Weights per row (GA stencil, Section 3.1): interpolated in the table at the
-row's own 1/G = f h / v.
+row's own 1/G = f h / v.  GAm (Section 3.1): the row's weights are the mean
+of the weights of the 27 stencil points, each looked up at its own 1/G.
+Reading: the mean runs over the stencil points inside the grid (at a grid
+edge the missing points carry no velocity).
+
+Mass, first form of Eq. 8 (``mass_form=1``): each of the 27 points enters
+with its own 1/kappa, i.e. the coefficient of neighbour j is
+(omega^2 / v_j^2) w_class(j) instead of (omega^2 / v_0^2) w_class(j).
+
+Pins of the variants (tests/test_oracle_operator_variants.py): on a constant
+model both reduce to the GA / second-form operator; with weights that do not
+depend on the row (the non-adaptive G4 / Gm stencils) and no PML, the first
+mass form is the transpose of the second (M1 = W diag(m) = (diag(m) W)^T
+with W symmetric); a pure-Python loop over rows and stencil points on tiny
+grids gives the same rows (GAm averages, class stencils of Eq. 4).
 
 Pins (tests/test_oracle_operator.py): interior symbol == m J - 2X/h^2 on a
 periodic box (Eq. vtilde, independent formulas); stiffness annihilates
@@ -75,12 +89,27 @@ def profiles_for(shape, h, npml, v_ref, r_coef):
             _pml.Profile1D.from_grid(nz, h, npml[4], npml[5], v_ref, r_coef))
 
 
-def row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows=None, beta=0.0):
+def _neighbour(v, ix, iy, iz, si, sj, sk):
+    """Velocity of stencil point (si, sj, sk) of each row and whether it lies
+    inside the grid (outside: the row's own velocity, never used)."""
+    nz, ny, nx = v.shape
+    jx, jy, jz = ix + si, iy + sj, iz + sk
+    ok = (jx >= 0) & (jx < nx) & (jy >= 0) & (jy < ny) & (jz >= 0) & (jz < nz)
+    vj = v[np.where(ok, jz, iz), np.where(ok, jy, iy), np.where(ok, jx, ix)].astype(np.float64)
+    return vj, ok
+
+
+def row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows=None, beta=0.0, weights="GA",
+                     mass_form=2):
     """27 complex coefficients for the requested rows.
 
-    v: float array (nz, ny, nx); rows: flat row indices (None = all rows).
+    v: float array (nz, ny, nx); rows: flat row indices (None = all rows);
+    weights: "GA" (the row's own G) or "GAm" (mean over the stencil points);
+    mass_form: 2 (kappa at the collocation point) or 1 (kappa at each point).
     Returns coef of shape (len(rows), 27) in OFFSETS order (dk, dj, di) and the
     validity mask (neighbour inside the grid)."""
+    if weights not in ("GA", "GAm") or mass_form not in (1, 2):
+        raise ValueError("weights must be GA or GAm, mass_form 1 or 2")
     nz, ny, nx = v.shape
     omega = 2.0 * np.pi * f
     if rows is None:
@@ -91,7 +120,16 @@ def row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows=None, beta=0.0)
     iz = rows // (nx * ny)
     v0 = v.reshape(-1)[rows].astype(np.float64)
 
-    w = _w.lookup(table, inv_g_nodes, f * h / v0)
+    if weights == "GA":
+        w = _w.lookup(table, inv_g_nodes, f * h / v0)
+    else:
+        acc = np.zeros((rows.size, 7))
+        cnt = np.zeros(rows.size)
+        for sk, sj, si in OFFSETS:
+            vj, ok = _neighbour(v, ix, iy, iz, si, sj, sk)
+            acc += np.where(ok[:, None], _w.lookup(table, inv_g_nodes, f * h / vj), 0.0)
+            cnt += ok
+        w = acc / cnt[:, None]
     ws1, ws2, ws3, wm1, wm2, wm3, wm4 = (w[:, k] for k in range(7))
     tw = (ws1 + 2.0 * ws2 / 3.0 + 0.5 * ws3, ws2 / 12.0, ws3 / 8.0)   # T_d weights
     mu = (wm1, wm2, wm3, wm4)                                        # mass per class
@@ -111,23 +149,27 @@ def row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows=None, beta=0.0)
     coef = np.zeros((rows.size, 27), dtype=np.complex128)
     valid = np.zeros((rows.size, 27), dtype=bool)
     for k, (sk, sj, si) in enumerate(OFFSETS):
+        mk = m
+        if mass_form == 1:
+            vj, _ = _neighbour(v, ix, iy, iz, si, sj, sk)
+            mk = (1.0 + 1j * beta) * omega ** 2 / vj ** 2
         c = (tw[abs(sj) + abs(sk)] * second(ux, dx, ix, si)
              + tw[abs(si) + abs(sk)] * second(uy, dy, iy, sj)
              + tw[abs(si) + abs(sj)] * second(uz, dz, iz, sk)
-             + m * mu[abs(si) + abs(sj) + abs(sk)])
+             + mk * mu[abs(si) + abs(sj) + abs(sk)])
         coef[:, k] = c
         valid[:, k] = ((ix + si >= 0) & (ix + si < nx) & (iy + sj >= 0) & (iy + sj < ny)
                        & (iz + sk >= 0) & (iz + sk < nz))
     return coef, valid
 
 
-def assemble_csr(v, h, f, profiles, table, inv_g_nodes, beta=0.0):
+def assemble_csr(v, h, f, profiles, table, inv_g_nodes, beta=0.0, weights="GA", mass_form=2):
     """The impedance matrix as scipy CSR (complex128), 27 entries per row
     (fewer at the grid edges)."""
     nz, ny, nx = v.shape
     N = nx * ny * nz
     rows = np.arange(N)
-    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta)
+    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta, weights, mass_form)
     cols = np.empty((N, 27), dtype=np.int64)
     for k, (sk, sj, si) in enumerate(OFFSETS):
         cols[:, k] = rows + si + nx * (sj + ny * sk)
@@ -137,11 +179,11 @@ def assemble_csr(v, h, f, profiles, table, inv_g_nodes, beta=0.0):
     return A
 
 
-def apply_rows(v, h, f, profiles, table, inv_g_nodes, x, rows, beta=0.0):
+def apply_rows(v, h, f, profiles, table, inv_g_nodes, x, rows, beta=0.0, weights="GA", mass_form=2):
     """(A x) at the requested rows only, x of shape (R, nz, ny, nx); returns
     (R, len(rows)).  Used to check full-size GPU applies on sampled outputs."""
     nz, ny, nx = v.shape
-    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta)
+    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta, weights, mass_form)
     rows = np.asarray(rows, dtype=np.int64)
     ix = rows % nx
     iy = (rows // nx) % ny
