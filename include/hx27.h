@@ -144,6 +144,25 @@ enum { HX_TABLE_BOTH = 0, HX_TABLE_OPERATOR = 1, HX_TABLE_PRECONDITIONER = 2 };
  * HX_ERR_STATE. */
 int hx_set_table_ex(hx_ctx* ctx, const double* table_host, int n_g, double d_inv_g, int which);
 
+/* Weights of an operator row (hx_set_operator_form). */
+enum { HX_WEIGHTS_GA = 0, HX_WEIGHTS_GAM = 1 };
+
+/* Operator variants of the paper for every later call on ctx that forms the
+ * operator itself (hx_apply_operator, hx_stencil_sweep, hx_row_coefficients,
+ * hx_assemble_csr, hx_assemble_csr_noalloc, and the Krylov operator and FP64
+ * residual of hx_solve; hx_solve's multigrid preconditioner stays GA with the
+ * second mass form, it only has to approximate A^-1):
+ *   weights   HX_WEIGHTS_GA (default): each row takes the weights of its own
+ *             G (Section 3.1, GA); HX_WEIGHTS_GAM: the mean of the weights of
+ *             the stencil points inside the grid, each at its own G (GAm);
+ *   mass_form 2 (default): the second form of Eq. 8, omega^2/kappa at the
+ *             collocation point; 1: the first form, omega^2/kappa_j at each
+ *             of the 27 points.
+ * A variant other than (GA, 2) runs on the one-thread-per-row kernels (the
+ * fields of a launch back to back), slower than the z-marching kernels.
+ * hx_apply_batched refuses variants.  Errors: HX_ERR_ARG. */
+int hx_set_operator_form(hx_ctx* ctx, int weights, int mass_form);
+
 /* ---------------------------------------------------------------- operator */
 
 /* Flag or-ed into hx_apply_operator's precision argument (see there). */

@@ -26,7 +26,7 @@ EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_
            "hx_assemble_csr_noalloc", "hx_kernel_config_info", "hx_set_kernel_config",
            "hx_autotune", "hx_stencil_sweep", "hx_server_create", "hx_server_submit",
            "hx_server_wait", "hx_server_get_stats", "hx_server_destroy", "hx_apply_batched",
-           "hx_fit_joint_weights", "hx_set_table_ex")
+           "hx_fit_joint_weights", "hx_set_table_ex", "hx_set_operator_form")
 
 NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
 APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
@@ -123,6 +123,7 @@ def lib():
     L.hx_last_error.restype = C.c_char_p
     L.hx_set_table.argtypes = [vp, dp, i, d]
     L.hx_set_table_ex.argtypes = [vp, dp, i, d, i]
+    L.hx_set_operator_form.argtypes = [vp, i, i]
     L.hx_apply_operator.argtypes = [vp, C.POINTER(hx_grid), vp, d, vp, vp, i, i, vp]
     L.hx_row_coefficients.argtypes = [vp, C.POINTER(hx_grid), vp, d, vp, vp]
     L.hx_assemble_csr.argtypes = [vp, C.POINTER(hx_grid), vp, d, C.POINTER(C.c_int64),
@@ -341,6 +342,11 @@ class Context:
         if check:
             self._check(st, "hx_solve")
         return rep.as_dict()
+
+    def set_operator_form(self, weights="GA", mass_form=2):
+        """hx_set_operator_form: weights "GA" or "GAm", mass_form 2 or 1."""
+        w = {"GA": 0, "GAm": 1}.get(weights, -1)
+        self._check(lib().hx_set_operator_form(self._h, w, int(mass_form)), "hx_set_operator_form")
 
     def set_kernel_config(self, cfg):
         """Force a complex64 kernel configuration (-1: automatic)."""

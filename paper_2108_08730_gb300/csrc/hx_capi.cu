@@ -157,6 +157,10 @@ OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double b
     d.plain_hi[a] = lv.hi[a];
   }
   d.cfg32 = ctx->st32_cfg;   // call sites that know nrhs refine this (ctx_cfg32)
+  if (!precond) {
+    d.gam = ctx->op_weights == HX_WEIGHTS_GAM;
+    d.mass1 = ctx->op_mass_form == 1;
+  }
   return d;
 }
 
@@ -318,6 +322,15 @@ cudaError_t upload_table(const double* table, int n_g, double** t64, float** t32
 }
 }  // namespace
 
+int hx_set_operator_form(hx_ctx* ctx, int weights, int mass_form) {
+  if (!ctx) return HX_ERR_ARG;
+  if (weights != HX_WEIGHTS_GA && weights != HX_WEIGHTS_GAM) return fail(ctx, HX_ERR_ARG, "unknown weights");
+  if (mass_form != 1 && mass_form != 2) return fail(ctx, HX_ERR_ARG, "mass_form must be 1 or 2");
+  ctx->op_weights = weights;
+  ctx->op_mass_form = mass_form;
+  return HX_OK;
+}
+
 int hx_set_table_ex(hx_ctx* ctx, const double* table, int n_g, double d_inv_g, int which) {
   if (!ctx) return HX_ERR_ARG;
   if (which < HX_TABLE_BOTH || which > HX_TABLE_PRECONDITIONER) return fail(ctx, HX_ERR_ARG, "unknown table role");
@@ -441,6 +454,8 @@ int hx_apply_batched(hx_ctx* ctx, const hx_apply_item* items, int n, double shif
   if (!items || n < 1 || n > (1 << 20)) return fail(ctx, HX_ERR_ARG, "need 1 <= n <= 2^20 items");
   if (!ctx->tab64) return fail(ctx, HX_ERR_STATE, "no weight table set (hx_set_table)");
   if (!std::isfinite(shift_beta)) return fail(ctx, HX_ERR_ARG, "shift_beta must be finite");
+  if (ctx->op_weights != HX_WEIGHTS_GA || ctx->op_mass_form != 2)
+    return fail(ctx, HX_ERR_STATE, "hx_apply_batched applies the GA operator with the second mass form only");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<GroupProb> probs(n);

@@ -12,49 +12,10 @@
 #include "hx_galerkin.cuh"
 #include "hx_internal.h"
 #include "hx_launch.cuh"
+#include "hx_row.cuh"
 
 namespace hx {
 namespace {
-
-template <typename T>
-__device__ __forceinline__ void fine_row(const OpDesc<T>& op, int ix, int iy, int iz,
-                                         typename CT<T>::type c[27]) {
-  using C = typename CT<T>::type;
-  const long long i = ix + (long long)op.nx * (iy + (long long)op.ny * iz);
-  const T vt = (T)__ldg(op.v + i);
-  const T iv = (T)1 / vt;
-  T u = op.u_scale * iv;
-  const T umax = (T)(op.n_g - 1);
-  u = u < (T)0 ? (T)0 : (u > umax ? umax : u);
-  int i0 = (int)u;
-  if (i0 > op.n_g - 2) i0 = op.n_g - 2;
-  const T t = u - (T)i0;
-  const T* a = op.tab + (size_t)i0 * kTabW;
-  T w[11];
-#pragma unroll
-  for (int k = 0; k < 11; ++k) w[k] = fma(t, __ldg(a + kTabW + k) - __ldg(a + k), __ldg(a + k));
-  const T m = op.omega2 * iv * iv;
-  const C mc = cmk(m, op.beta * m);
-  const T tw[3] = {w[8], w[9], w[10]};
-  const int id[3] = {ix, iy, iz};
-  C D[3][3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const T* q = op.axis[d] + 4 * (size_t)id[d];
-    const C up = cmk(__ldg(q), __ldg(q + 1)), dn = cmk(__ldg(q + 2), __ldg(q + 3));
-    D[d][2] = up;
-    D[d][0] = dn;
-    D[d][1] = cmk(-(up.x + dn.x), -(up.y + dn.y));
-  }
-#pragma unroll
-  for (int k = 0; k < 27; ++k) {
-    const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dk = k / 9 - 1;
-    C v = cscale(tw[abs(dj) + abs(dk)], D[0][di + 1]);
-    v = cfmar(tw[abs(di) + abs(dk)], D[1][dj + 1], v);
-    v = cfmar(tw[abs(di) + abs(dj)], D[2][dk + 1], v);
-    c[k] = cfma(mc, cmk(w[4 + abs(di) + abs(dj) + abs(dk)], (T)0), v);
-  }
-}
 
 // trilinear weight of fine offset r (relative to 2I, in [-2, 2]) for coarse
 // offset D in {-1, 0, 1}

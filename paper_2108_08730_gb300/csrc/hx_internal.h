@@ -41,6 +41,10 @@ struct OpDesc {
   const T* axis[3];        // per axis: [n][4] = (up.re, up.im, dn.re, dn.im)
   int plain_lo[3], plain_hi[3];  // nodes whose up = dn = 1/h^2 exactly
   int cfg32 = -1;          // complex64 kernel configuration (-1: automatic)
+  // operator variants (Section 3.1 GAm weights, first mass form of Eq. 8);
+  // descriptors with either set run on the one-thread-per-row kernels
+  int gam = 0;             // 1: row weights = mean over the in-grid stencil points
+  int mass1 = 0;           // 1: mass term with omega^2 / v_j^2 at each stencil point
 };
 
 enum StencilMode { kApply = 0, kResidual = 1, kJacobi = 2, kJacobi0 = 3 };

@@ -27,7 +27,9 @@
 
 #include "hx_complex.cuh"
 #include "hx_internal.h"
+#include "hx_galerkin.cuh"
 #include "hx_launch.cuh"
+#include "hx_row.cuh"
 
 namespace hx {
 namespace {
@@ -421,7 +423,8 @@ __global__ void jacobi0_kernel(OpDesc<T> op, const typename CT<T>::type* __restr
   }
 }
 
-// One thread per row: the 27 coefficients in (dk, dj, di) order, FP64.
+// One thread per row: the 27 coefficients in (dk, dj, di) order, FP64
+// (entries whose neighbour lies outside the grid are 0).
 __global__ void row_coef_kernel(OpDesc<double> op, double2* __restrict__ coef) {
   pdl_enter();
   const long long N = (long long)op.nx * op.ny * op.nz;
@@ -430,35 +433,14 @@ __global__ void row_coef_kernel(OpDesc<double> op, double2* __restrict__ coef) {
     const int ix = (int)(i % op.nx);
     const int iy = (int)((i / op.nx) % op.ny);
     const int iz = (int)(i / ((long long)op.nx * op.ny));
-    const PointW<double> pw = point_weights(op, op.tab, op.v[i]);
-    const double tw[3] = {pw.w[8], pw.w[9], pw.w[10]};
-    const double2 mc = make_double2(pw.m, op.beta * pw.m);
-    const int id[3] = {ix, iy, iz};
-    const int n[3] = {op.nx, op.ny, op.nz};
-    double2 D[3][3];   // D[axis][s+1]
-    for (int d = 0; d < 3; ++d) {
-      const double* q = op.axis[d] + 4 * (size_t)id[d];
-      const double2 up = make_double2(q[0], q[1]), dn = make_double2(q[2], q[3]);
-      D[d][2] = up;
-      D[d][0] = dn;
-      D[d][1] = make_double2(-(up.x + dn.x), -(up.y + dn.y));
+    double2 c[27];
+    fine_row<double>(op, ix, iy, iz, c);
+    for (int k = 0; k < 27; ++k) {
+      const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dk = k / 9 - 1;
+      const bool inside = ix + di >= 0 && ix + di < op.nx && iy + dj >= 0 && iy + dj < op.ny &&
+                          iz + dk >= 0 && iz + dk < op.nz;
+      coef[i * 27 + k] = inside ? c[k] : make_double2(0.0, 0.0);
     }
-    int k = 0;
-    for (int dk = -1; dk <= 1; ++dk)
-      for (int dj = -1; dj <= 1; ++dj)
-        for (int di = -1; di <= 1; ++di, ++k) {
-          const int o[3] = {di, dj, dk};
-          bool inside = true;
-          for (int d = 0; d < 3; ++d) inside = inside && id[d] + o[d] >= 0 && id[d] + o[d] < n[d];
-          double2 c = make_double2(0.0, 0.0);
-          if (inside) {
-            c = cfmar(tw[abs(dj) + abs(dk)], D[0][di + 1], c);
-            c = cfmar(tw[abs(di) + abs(dk)], D[1][dj + 1], c);
-            c = cfmar(tw[abs(di) + abs(dj)], D[2][dk + 1], c);
-            c = cfma(mc, make_double2(pw.w[4 + abs(di) + abs(dj) + abs(dk)], 0.0), c);
-          }
-          coef[i * 27 + k] = c;
-        }
   }
 }
 
@@ -543,6 +525,11 @@ cudaError_t launch_m(const OpDesc<T>& op, const void* x, const void* b, void* y,
 template <typename T>
 cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const void* b, void* y,
                            int nrhs, long long rstride, double omega_j, cudaStream_t s) {
+  // operator variants: the one-thread-per-row kernel (fields back to back)
+  if (op.gam || op.mass1) {
+    if (rstride != (long long)op.nx * op.ny * op.nz) return cudaErrorInvalidValue;
+    return launch_direct_stencil<T>(op, mode, x, b, y, nrhs, omega_j, s);
+  }
   // the complex64 kernel's bulk row copies need a 16-byte aligned x
   if (sizeof(T) == 4 && mode != kJacobi0 && ((uintptr_t)x & 15) == 0) {
     const int cfg = op.cfg32 >= 0 && op.cfg32 < st32_num_configs() ? op.cfg32 : st32_default_config(nrhs);
