@@ -471,6 +471,7 @@ int hx_apply_batched(hx_ctx* ctx, const hx_apply_item* items, int n, double shif
     const int nl[3] = {it.grid.nx, it.grid.ny, it.grid.nz};
     if ((st = get_level(ctx, &it.grid, nl, it.grid.h, &lv))) return st;
     probs[i].op = make_desc<float>(ctx, *lv, it.v_dev, shift_beta);
+    probs[i].op.xshift = st32_xshift(probs[i].op);
     probs[i].x = it.x_dev;
     probs[i].y = it.y_dev;
     probs[i].nrhs = it.nrhs;

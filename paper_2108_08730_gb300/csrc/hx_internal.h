@@ -43,6 +43,7 @@ struct OpDesc {
   int cfg32 = -1;          // complex64 kernel configuration (-1: automatic)
   // operator variants (Section 3.1 GAm weights, first mass form of Eq. 8);
   // descriptors with either set run on the one-thread-per-row kernels
+  int xshift = 0;          // complex64 kernel: x-tile origin at -xshift (st32_xshift)
   int gam = 0;             // 1: row weights = mean over the in-grid stencil points
   int mass1 = 0;           // 1: mass term with omega^2 / v_j^2 at each stencil point
 };
@@ -62,6 +63,10 @@ cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const v
 int st32_num_configs();
 cudaError_t launch_stencil32(const OpDesc<float>& op, int mode, int cfg, const void* x, const void* b,
                              void* y, int nrhs, long long rstride, double omega_j, cudaStream_t s);
+// Origin shift of the complex64 kernel's 32-wide x-tiles: the shift in
+// [0, 32 ceil(nx/32) - nx] (so the tile count is unchanged) that leaves the
+// fewest tiles holding x-PML columns; such tiles take the general PML form.
+int st32_xshift(const OpDesc<float>& op);
 // Automatic choice of the complex64 configuration for nrhs fields.
 int st32_default_config(int nrhs);
 

@@ -136,18 +136,27 @@ struct Cfg {
 template <int MODE, int YB, int RB>
 __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2* __restrict__ x,
                                           const float2* __restrict__ b, float2* __restrict__ y,
-                                          int nrhs, long long rstride, int zchunk, float omega_j,
-                                          int tbx, int tby, int tbz, float2* ring) {
+                                          int nrhs, long long rstride, int zchunk, int zmul,
+                                          float omega_j, int tbx, int tby, int tbz, float2* ring) {
   using K = Cfg<YB, RB>;
   constexpr unsigned SLOTB = K::SLOTB, RINGB = K::NSLOT * K::SLOTB;
   const int tid = threadIdx.x, tx = tid & 31, w = tid >> 5;
   const int nx = op.nx, ny = op.ny, nz = op.nz;
-  const int gx0 = tbx * kW, gy0 = tby * K::TY;
+  const int gx0 = tbx * kW - op.xshift, gy0 = tby * K::TY;   // gx0 may be negative (tile 0)
   const int ix = gx0 + tx, iyb = gy0 + w * YB;
   const int nrb = (nrhs + RB - 1) / RB;
   const int rblk = tbz % nrb, zc = tbz / nrb;
   const int r0 = rblk * RB, rcount = min(RB, nrhs - r0);
-  const int z0 = zc * zchunk, z1 = min(nz, z0 + zchunk);
+  // Tiles holding no x/y-PML row march zmul times longer z-chunks: their
+  // planes cost about half as much, so all CTAs of a launch end together.
+  int zlen = zchunk;
+  if (zmul > 1) {
+    const int xa = max(gx0, 0), xb = min(gx0 + kW - 1, nx - 1), yb = min(gy0 + K::TY - 1, ny - 1);
+    if (xa >= op.plain_lo[0] && xb <= op.plain_hi[0] && gy0 >= op.plain_lo[1] && yb <= op.plain_hi[1])
+      zlen = zchunk * zmul;
+  }
+  const int z0 = zc * zlen, z1 = min(nz, z0 + zlen);
+  if (z0 >= nz) return;                                // a chunk index past a long-chunk tile's end
   const long long plane = (long long)nx * ny;
   const bool shift = op.beta != 0.f;
 
@@ -229,7 +238,7 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
   // byte offsets of the slots of planes z-1, z, z+1 and of the next issue
   unsigned o_m = 0, o_0 = SLOTB, o_p = 2 * SLOTB, o_i = (K::D + 2) * SLOTB;
 
-  const bool xin = ix < nx;
+  const bool xin = ix >= 0 && ix < nx;
   const bool plain_x = ix >= op.plain_lo[0] && ix <= op.plain_hi[0];
   const float umax = (float)(op.n_g - 1);
   const float ih2 = op.inv_h2;
@@ -459,10 +468,11 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
 template <int MODE, int YB, int RB>
 __global__ void __launch_bounds__(kThr, Cfg<YB, RB>::MINB)
 st32_kernel(const OpDesc<float> op, const float2* __restrict__ x, const float2* __restrict__ b,
-            float2* __restrict__ y, int nrhs, long long rstride, int zchunk, float omega_j) {
+            float2* __restrict__ y, int nrhs, long long rstride, int zchunk, int zmul, float omega_j) {
   pdl_enter();
   extern __shared__ __align__(16) float2 ring[];       // [NSLOT][RB][PH][kPW]
-  st32_tile<MODE, YB, RB>(op, x, b, y, nrhs, rstride, zchunk, omega_j, blockIdx.x, blockIdx.y, blockIdx.z, ring);
+  st32_tile<MODE, YB, RB>(op, x, b, y, nrhs, rstride, zchunk, zmul, omega_j, blockIdx.x, blockIdx.y,
+                          blockIdx.z, ring);
 }
 
 // Persistent form over a list of problems of different sizes: each CTA takes
@@ -489,7 +499,7 @@ st32_group_kernel(const GroupProb* __restrict__ probs, const GroupItem* __restri
       __syncthreads();
       cur = it.prob;
     }
-    st32_tile<kApply, YB, RB>(P.op, (const float2*)P.x, nullptr, (float2*)P.y, P.nrhs, P.rstride, P.zchunk,
+    st32_tile<kApply, YB, RB>(P.op, (const float2*)P.x, nullptr, (float2*)P.y, P.nrhs, P.rstride, P.zchunk, 1,
                               0.f, it.bx, it.by, it.bz, ring);
   }
 }
@@ -509,6 +519,29 @@ int pick_zchunk32(int nz, long long ntiles_xy, int nrb, int slots, int prologue)
     if (cost < best_cost * 0.999) {
       best_cost = cost;
       best = zc;
+    }
+  }
+  return best;
+}
+
+// The same with tiles of two costs: n_gen tiles holding x/y-PML rows (about
+// twice the per-plane cost) march zg planes per CTA, the n_cln others zmul zg;
+// minimise waves x the longest CTA (in interior-plane units).  Returns zg.
+int pick_zchunk32_bal(int nz, long long n_gen, long long n_cln, int nrb, int slots, int prologue, int zmul) {
+  int best = nz;
+  double best_cost = 1e300;
+  for (int zg = nz; zg >= 3; --zg) {
+    const long long nzg = (nz + zg - 1) / zg;
+    if ((nz + nzg - 1) / nzg != zg) continue;
+    if (nzg * nrb > 65535) break;
+    const long long zc = std::min<long long>((long long)zmul * zg, nz), nzc = (nz + zc - 1) / zc;
+    const long long ctas = (n_gen * nzg + n_cln * nzc) * nrb;
+    const long long waves = (ctas + slots - 1) / slots;
+    const double t = std::max(2.0 * zg, (double)zc) + prologue;
+    const double cost = (double)waves * t;
+    if (cost < best_cost * 0.999) {
+      best_cost = cost;
+      best = zg;
     }
   }
   return best;
@@ -534,13 +567,29 @@ cudaError_t launch_cfg(const OpDesc<float>& op, const void* x, const void* b, vo
   }
   const int bx = (op.nx + kW - 1) / kW, by = (op.ny + K::TY - 1) / K::TY;
   const int nrb = (nrhs + RB - 1) / RB;
-  int zchunk = pick_zchunk32(op.nz, (long long)bx * by, nrb, g_num_sms * K::MINB, K::D + 2);
+  // tiles holding x/y-PML rows (the same test as in st32_tile)
+  long long gen_x = 0, gen_y = 0;
+  for (int t = 0; t < bx; ++t) {
+    const int xa = std::max(t * kW - op.xshift, 0), xb = std::min(t * kW - op.xshift + kW - 1, op.nx - 1);
+    gen_x += xa < op.plain_lo[0] || xb > op.plain_hi[0];
+  }
+  for (int t = 0; t < by; ++t) {
+    const int ya = t * K::TY, yb = std::min(ya + K::TY - 1, op.ny - 1);
+    gen_y += ya < op.plain_lo[1] || yb > op.plain_hi[1];
+  }
+  const long long n_cln = (long long)(bx - gen_x) * (by - gen_y), n_gen = (long long)bx * by - n_cln;
+  const long long slots = (long long)g_num_sms * K::MINB;
+  int zchunk = pick_zchunk32(op.nz, (long long)bx * by, nrb, (int)slots, K::D + 2);
+  const long long waves = ((op.nz + zchunk - 1) / zchunk * nrb * bx * by + slots - 1) / slots;
+  // with a few waves the longest CTA sets the time: balance the two tile
+  // kinds; with more waves the CTA scheduler balances by itself
+  const int zmul = n_gen > 0 && n_cln > 0 && waves <= 2 ? 2 : 1;
+  if (zmul > 1) zchunk = pick_zchunk32_bal(op.nz, n_gen, n_cln, nrb, (int)slots, K::D + 2, zmul);
   if (HX_ST32_ZMAX > 0 && zchunk > HX_ST32_ZMAX) zchunk = (op.nz + (op.nz + HX_ST32_ZMAX - 1) / HX_ST32_ZMAX - 1) / ((op.nz + HX_ST32_ZMAX - 1) / HX_ST32_ZMAX);
   const long long gz = (long long)((op.nz + zchunk - 1) / zchunk) * nrb;
   if (gz > 65535) return cudaErrorInvalidConfiguration;
   (void)launch_k(kern, dim3(bx, by, (unsigned)gz), kThr, K::SMEM, s, op, (const float2*)x, (const float2*)b,
-                                                          (float2*)y, nrhs, rstride, zchunk,
-                                                          (float)omega_j);
+                 (float2*)y, nrhs, rstride, zchunk, zmul, (float)omega_j);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -638,8 +687,28 @@ cudaError_t launch_stencil32_group(int cfg, const GroupProb* probs_dev, const Gr
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_stencil32(const OpDesc<float>& op, int mode, int cfg, const void* x, const void* b,
+int st32_xshift(const OpDesc<float>& op) {
+  const int ntiles = (op.nx + kW - 1) / kW, smax = ntiles * kW - op.nx;
+  if (op.plain_lo[0] > op.plain_hi[0]) return 0;   // every column stretched
+  int best = 0, best_n = ntiles + 1;
+  for (int sh = 0; sh <= smax; ++sh) {
+    int n = 0;
+    for (int t = 0; t < ntiles; ++t) {
+      const int lo = std::max(t * kW - sh, 0), hi = std::min(t * kW - sh + kW - 1, op.nx - 1);
+      if (lo < op.plain_lo[0] || hi > op.plain_hi[0]) ++n;
+    }
+    if (n < best_n) {
+      best_n = n;
+      best = sh;
+    }
+  }
+  return best;
+}
+
+cudaError_t launch_stencil32(const OpDesc<float>& op_in, int mode, int cfg, const void* x, const void* b,
                              void* y, int nrhs, long long rstride, double omega_j, cudaStream_t s) {
+  OpDesc<float> op = op_in;
+  op.xshift = st32_xshift(op);
   switch (mode) {
     case kApply: return launch_mode<kApply>(op, cfg, x, b, y, nrhs, rstride, omega_j, s);
     case kResidual: return launch_mode<kResidual>(op, cfg, x, b, y, nrhs, rstride, omega_j, s);
