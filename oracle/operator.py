@@ -44,6 +44,20 @@ Mass, first form of Eq. 8 (``mass_form=1``): each of the 27 points enters
 with its own 1/kappa, i.e. the coefficient of neighbour j is
 (omega^2 / v_j^2) w_class(j) instead of (omega^2 / v_0^2) w_class(j).
 
+Heterogeneous density and attenuation (Eq. 2, Eqs. 1.1-1.4; the paper's
+benchmarks keep b = 1 and no attenuation): with buoyancy b = 1/rho
+each stretched second difference becomes the conservative form
+  [b(i+1/2)(p(i+1)-p(i))/xi(i+1/2) - b(i-1/2)(p(i)-p(i-1))/xi(i-1/2)] / (xi(i) h^2)
+on its own stencil line, b at a half node the mean of its two nodes (b at the
+node where the other lies outside the grid); the mass omega^2/kappa becomes
+omega^2 b / c*^2 with the complex velocity c* = v (1 - i/(2Q)), so plane waves
+decay as exp(-Im(k) r) for exp(-i omega t).  The weights stay those of the
+real G = v / (f h).  Pins (tests/test_oracle_medium.py): b = 1 and 1/Q = 0
+give the operator above; a constant b scales A; the 7-point weights give the
+textbook variable-coefficient Laplacian D^T diag(b_half) D assembled from
+difference matrices; an attenuated homogeneous solve decays at the rate of
+the complex wavenumber.
+
 Pins of the variants (tests/test_oracle_operator_variants.py): on a constant
 model both reduce to the GA / second-form operator; with weights that do not
 depend on the row (the non-adaptive G4 / Gm stencils) and no PML, the first
@@ -99,13 +113,33 @@ def _neighbour(v, ix, iy, iz, si, sj, sk):
     return vj, ok
 
 
+def _field_at(a, jx, jy, jz):
+    """a at (jx, jy, jz) with the indices clamped into the grid."""
+    nz, ny, nx = a.shape
+    return a[np.clip(jz, 0, nz - 1), np.clip(jy, 0, ny - 1), np.clip(jx, 0, nx - 1)].astype(np.float64)
+
+
+def _half_buoyancy(b, px, py, pz, d, s):
+    """b at the half node between point p and its neighbour p + s e_d (Eq. 2
+    with heterogeneous buoyancy).  Reading: the arithmetic mean of the two
+    nodes; where the neighbour lies outside the grid, b at p."""
+    nz, ny, nx = b.shape
+    q = [px, py, pz]
+    q[d] = q[d] + s
+    inside = (q[0] >= 0) & (q[0] < nx) & (q[1] >= 0) & (q[1] < ny) & (q[2] >= 0) & (q[2] < nz)
+    bp = _field_at(b, px, py, pz)
+    return np.where(inside, 0.5 * (bp + _field_at(b, q[0], q[1], q[2])), bp)
+
+
 def row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows=None, beta=0.0, weights="GA",
-                     mass_form=2):
+                     mass_form=2, buoyancy=None, inv_q=None):
     """27 complex coefficients for the requested rows.
 
     v: float array (nz, ny, nx); rows: flat row indices (None = all rows);
     weights: "GA" (the row's own G) or "GAm" (mean over the stencil points);
-    mass_form: 2 (kappa at the collocation point) or 1 (kappa at each point).
+    mass_form: 2 (kappa at the collocation point) or 1 (kappa at each point);
+    buoyancy: b = 1/rho per node (None: 1, the paper's benchmarks);
+    inv_q: 1/Q per node (None: 0, no attenuation).
     Returns coef of shape (len(rows), 27) in OFFSETS order (dk, dj, di) and the
     validity mask (neighbour inside the grid)."""
     if weights not in ("GA", "GAm") or mass_form not in (1, 2):
@@ -133,7 +167,18 @@ def row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows=None, beta=0.0,
     ws1, ws2, ws3, wm1, wm2, wm3, wm4 = (w[:, k] for k in range(7))
     tw = (ws1 + 2.0 * ws2 / 3.0 + 0.5 * ws3, ws2 / 12.0, ws3 / 8.0)   # T_d weights
     mu = (wm1, wm2, wm3, wm4)                                        # mass per class
-    m = (1.0 + 1j * beta) * omega ** 2 / v0 ** 2
+
+    def mass_at(jx, jy, jz, vj):
+        # omega^2 / kappa* with kappa* = rho c*^2, c* = v (1 - i/(2Q)) (decay
+        # for exp(-i omega t)); (1 + i beta) for the shifted operator
+        mj = (1.0 + 1j * beta) * omega ** 2 / vj ** 2
+        if buoyancy is not None:
+            mj = mj * _field_at(buoyancy, jx, jy, jz)
+        if inv_q is not None:
+            mj = mj / (1.0 - 0.5j * _field_at(inv_q, jx, jy, jz)) ** 2
+        return mj
+
+    m = mass_at(ix, iy, iz, v0)
 
     ux, dx = axis_coefficients(profiles[0], nx, h, omega)
     uy, dy = axis_coefficients(profiles[1], ny, h, omega)
@@ -148,14 +193,29 @@ def row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows=None, beta=0.0,
 
     coef = np.zeros((rows.size, 27), dtype=np.complex128)
     valid = np.zeros((rows.size, 27), dtype=bool)
+    def second_b(up, dn, i, s, d, line):
+        # the same along axis d on the stencil line through point `line`
+        # (buoyancy at the line's half nodes)
+        bp = _half_buoyancy(buoyancy, *line, d, +1)
+        bm = _half_buoyancy(buoyancy, *line, d, -1)
+        if s == 1:
+            return up[i] * bp
+        if s == -1:
+            return dn[i] * bm
+        return -(up[i] * bp + dn[i] * bm)
+
     for k, (sk, sj, si) in enumerate(OFFSETS):
         mk = m
         if mass_form == 1:
             vj, _ = _neighbour(v, ix, iy, iz, si, sj, sk)
-            mk = (1.0 + 1j * beta) * omega ** 2 / vj ** 2
-        c = (tw[abs(sj) + abs(sk)] * second(ux, dx, ix, si)
-             + tw[abs(si) + abs(sk)] * second(uy, dy, iy, sj)
-             + tw[abs(si) + abs(sj)] * second(uz, dz, iz, sk)
+            mk = mass_at(ix + si, iy + sj, iz + sk, vj)
+        if buoyancy is None:
+            sx, sy, sz = second(ux, dx, ix, si), second(uy, dy, iy, sj), second(uz, dz, iz, sk)
+        else:
+            sx = second_b(ux, dx, ix, si, 0, (ix, iy + sj, iz + sk))
+            sy = second_b(uy, dy, iy, sj, 1, (ix + si, iy, iz + sk))
+            sz = second_b(uz, dz, iz, sk, 2, (ix + si, iy + sj, iz))
+        c = (tw[abs(sj) + abs(sk)] * sx + tw[abs(si) + abs(sk)] * sy + tw[abs(si) + abs(sj)] * sz
              + mk * mu[abs(si) + abs(sj) + abs(sk)])
         coef[:, k] = c
         valid[:, k] = ((ix + si >= 0) & (ix + si < nx) & (iy + sj >= 0) & (iy + sj < ny)
@@ -163,13 +223,15 @@ def row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows=None, beta=0.0,
     return coef, valid
 
 
-def assemble_csr(v, h, f, profiles, table, inv_g_nodes, beta=0.0, weights="GA", mass_form=2):
+def assemble_csr(v, h, f, profiles, table, inv_g_nodes, beta=0.0, weights="GA", mass_form=2,
+                 buoyancy=None, inv_q=None):
     """The impedance matrix as scipy CSR (complex128), 27 entries per row
     (fewer at the grid edges)."""
     nz, ny, nx = v.shape
     N = nx * ny * nz
     rows = np.arange(N)
-    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta, weights, mass_form)
+    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta, weights, mass_form,
+                                   buoyancy, inv_q)
     cols = np.empty((N, 27), dtype=np.int64)
     for k, (sk, sj, si) in enumerate(OFFSETS):
         cols[:, k] = rows + si + nx * (sj + ny * sk)
@@ -179,11 +241,13 @@ def assemble_csr(v, h, f, profiles, table, inv_g_nodes, beta=0.0, weights="GA", 
     return A
 
 
-def apply_rows(v, h, f, profiles, table, inv_g_nodes, x, rows, beta=0.0, weights="GA", mass_form=2):
+def apply_rows(v, h, f, profiles, table, inv_g_nodes, x, rows, beta=0.0, weights="GA", mass_form=2,
+               buoyancy=None, inv_q=None):
     """(A x) at the requested rows only, x of shape (R, nz, ny, nx); returns
     (R, len(rows)).  Used to check full-size GPU applies on sampled outputs."""
     nz, ny, nx = v.shape
-    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta, weights, mass_form)
+    coef, valid = row_coefficients(v, h, f, profiles, table, inv_g_nodes, rows, beta, weights, mass_form,
+                                   buoyancy, inv_q)
     rows = np.asarray(rows, dtype=np.int64)
     ix = rows % nx
     iy = (rows // nx) % ny
