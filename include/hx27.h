@@ -163,6 +163,25 @@ enum { HX_WEIGHTS_GA = 0, HX_WEIGHTS_GAM = 1 };
  * hx_apply_batched refuses variants.  Errors: HX_ERR_ARG. */
 int hx_set_operator_form(hx_ctx* ctx, int weights, int mass_form);
 
+/* Heterogeneous density and attenuation (Eq. 2 and Eqs. 1.1-1.4; the paper's
+ * benchmarks use b = 1 and no attenuation, Section 3.1) for every later call
+ * on ctx that forms the operator itself (the calls listed under
+ * hx_set_operator_form; hx_solve's preconditioner keeps b = 1, no Q):
+ *   buoyancy_dev: float32 [nz][ny][nx] b = 1/rho per node, > 0, in any unit
+ *                 (the operator is linear in b); NULL = 1.  Each second
+ *                 difference becomes the conservative form with b at the half
+ *                 nodes (the mean of the two nodes; the node's own b where the
+ *                 other lies outside the grid) and the mass omega^2 b / v^2;
+ *   inv_q_dev:    float32 [nz][ny][nx] 1/Q per node, >= 0; NULL = no
+ *                 attenuation.  The velocity becomes c* = v (1 - i/(2Q)), so
+ *                 waves decay as exp(-Im(omega/c*) r) (exp(-i omega t)); the
+ *                 weights still follow the real G = v / (f h).
+ * The arrays are caller-owned and read by those calls with the call's grid
+ * size: keep them alive and sized for every grid used until
+ * hx_set_medium(ctx, NULL, NULL).  A medium runs on the one-thread-per-row
+ * kernels; hx_apply_batched refuses it.  Errors: HX_ERR_ARG (null ctx). */
+int hx_set_medium(hx_ctx* ctx, const float* buoyancy_dev, const float* inv_q_dev);
+
 /* ---------------------------------------------------------------- operator */
 
 /* Flag or-ed into hx_apply_operator's precision argument (see there). */

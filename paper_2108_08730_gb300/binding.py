@@ -26,7 +26,8 @@ EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_
            "hx_assemble_csr_noalloc", "hx_kernel_config_info", "hx_set_kernel_config",
            "hx_autotune", "hx_stencil_sweep", "hx_server_create", "hx_server_submit",
            "hx_server_wait", "hx_server_get_stats", "hx_server_destroy", "hx_apply_batched",
-           "hx_fit_joint_weights", "hx_set_table_ex", "hx_set_operator_form")
+           "hx_fit_joint_weights", "hx_set_table_ex", "hx_set_operator_form",
+           "hx_set_medium")
 
 NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
 APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
@@ -124,6 +125,7 @@ def lib():
     L.hx_set_table.argtypes = [vp, dp, i, d]
     L.hx_set_table_ex.argtypes = [vp, dp, i, d, i]
     L.hx_set_operator_form.argtypes = [vp, i, i]
+    L.hx_set_medium.argtypes = [vp, vp, vp]
     L.hx_apply_operator.argtypes = [vp, C.POINTER(hx_grid), vp, d, vp, vp, i, i, vp]
     L.hx_row_coefficients.argtypes = [vp, C.POINTER(hx_grid), vp, d, vp, vp]
     L.hx_assemble_csr.argtypes = [vp, C.POINTER(hx_grid), vp, d, C.POINTER(C.c_int64),
@@ -347,6 +349,13 @@ class Context:
         """hx_set_operator_form: weights "GA" or "GAm", mass_form 2 or 1."""
         w = {"GA": 0, "GAm": 1}.get(weights, -1)
         self._check(lib().hx_set_operator_form(self._h, w, int(mass_form)), "hx_set_operator_form")
+
+    def set_medium(self, buoyancy=None, inv_q=None):
+        """hx_set_medium: float32 CUDA tensors (nz, ny, nx) of b = 1/rho and
+        1/Q, or None.  The tensors are kept referenced until the next call."""
+        self._medium = (buoyancy, inv_q)
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+        self._check(lib().hx_set_medium(self._h, ptr(buoyancy), ptr(inv_q)), "hx_set_medium")
 
     def set_kernel_config(self, cfg):
         """Force a complex64 kernel configuration (-1: automatic)."""

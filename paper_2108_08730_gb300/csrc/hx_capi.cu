@@ -160,6 +160,8 @@ OpDesc<T> make_desc(const hx_ctx* ctx, const Level& lv, const float* v, double b
   if (!precond) {
     d.gam = ctx->op_weights == HX_WEIGHTS_GAM;
     d.mass1 = ctx->op_mass_form == 1;
+    d.buoy = ctx->med_buoy;
+    d.invq = ctx->med_invq;
   }
   return d;
 }
@@ -331,6 +333,13 @@ int hx_set_operator_form(hx_ctx* ctx, int weights, int mass_form) {
   return HX_OK;
 }
 
+int hx_set_medium(hx_ctx* ctx, const float* buoyancy_dev, const float* inv_q_dev) {
+  if (!ctx) return HX_ERR_ARG;
+  ctx->med_buoy = buoyancy_dev;
+  ctx->med_invq = inv_q_dev;
+  return HX_OK;
+}
+
 int hx_set_table_ex(hx_ctx* ctx, const double* table, int n_g, double d_inv_g, int which) {
   if (!ctx) return HX_ERR_ARG;
   if (which < HX_TABLE_BOTH || which > HX_TABLE_PRECONDITIONER) return fail(ctx, HX_ERR_ARG, "unknown table role");
@@ -454,8 +463,9 @@ int hx_apply_batched(hx_ctx* ctx, const hx_apply_item* items, int n, double shif
   if (!items || n < 1 || n > (1 << 20)) return fail(ctx, HX_ERR_ARG, "need 1 <= n <= 2^20 items");
   if (!ctx->tab64) return fail(ctx, HX_ERR_STATE, "no weight table set (hx_set_table)");
   if (!std::isfinite(shift_beta)) return fail(ctx, HX_ERR_ARG, "shift_beta must be finite");
-  if (ctx->op_weights != HX_WEIGHTS_GA || ctx->op_mass_form != 2)
-    return fail(ctx, HX_ERR_STATE, "hx_apply_batched applies the GA operator with the second mass form only");
+  if (ctx->op_weights != HX_WEIGHTS_GA || ctx->op_mass_form != 2 || ctx->med_buoy || ctx->med_invq)
+    return fail(ctx, HX_ERR_STATE,
+                "hx_apply_batched applies the GA operator with the second mass form and b = 1, no Q only");
   cudaSetDevice(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
   std::vector<GroupProb> probs(n);

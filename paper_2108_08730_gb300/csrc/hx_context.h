@@ -55,6 +55,8 @@ struct hx_ctx {
   int st32_cfg = -1;            // forced complex64 kernel configuration (-1: automatic)
   int op_weights = 0;           // HX_WEIGHTS_GA / HX_WEIGHTS_GAM (hx_set_operator_form)
   int op_mass_form = 2;         // 2 or 1 (hx_set_operator_form)
+  const float* med_buoy = nullptr;   // hx_set_medium: caller-owned device arrays
+  const float* med_invq = nullptr;
   std::map<std::string, int> tuned;   // hx_autotune choices by grid size and nrhs
   // cached levels, keyed by their defining parameters
   std::map<std::string, std::unique_ptr<hx::Level>> levels;

@@ -46,6 +46,10 @@ struct OpDesc {
   int xshift = 0;          // complex64 kernel: x-tile origin at -xshift (st32_xshift)
   int gam = 0;             // 1: row weights = mean over the in-grid stencil points
   int mass1 = 0;           // 1: mass term with omega^2 / v_j^2 at each stencil point
+  // heterogeneous medium (Eq. 2): buoyancy b = 1/rho and 1/Q per node of this
+  // grid, or null (b = 1, no attenuation); set only on the operator itself
+  const float* buoy = nullptr;
+  const float* invq = nullptr;
 };
 
 enum StencilMode { kApply = 0, kResidual = 1, kJacobi = 2, kJacobi0 = 3 };

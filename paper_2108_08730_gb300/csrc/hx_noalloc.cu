@@ -112,6 +112,8 @@ extern "C" int hx_assemble_csr_noalloc(hx_ctx* ctx, const hx_grid* grid, const f
   d.inv_h2 = ih2;
   d.gam = ctx->op_weights == HX_WEIGHTS_GAM;
   d.mass1 = ctx->op_mass_form == 1;
+  d.buoy = ctx->med_buoy;
+  d.invq = ctx->med_invq;
   for (int a = 0; a < 3; ++a) {
     const Profile1D prof = Profile1D::from_grid(n[a], grid->h, grid->npml[2 * a], grid->npml[2 * a + 1],
                                                 grid->v_ref, grid->r_coef);

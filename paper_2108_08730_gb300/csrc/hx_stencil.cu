@@ -525,8 +525,9 @@ cudaError_t launch_m(const OpDesc<T>& op, const void* x, const void* b, void* y,
 template <typename T>
 cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const void* b, void* y,
                            int nrhs, long long rstride, double omega_j, cudaStream_t s) {
-  // operator variants: the one-thread-per-row kernel (fields back to back)
-  if (op.gam || op.mass1) {
+  // operator variants and heterogeneous media: the one-thread-per-row kernel
+  // (fields back to back)
+  if (op.gam || op.mass1 || op.buoy || op.invq) {
     if (rstride != (long long)op.nx * op.ny * op.nz) return cudaErrorInvalidValue;
     return launch_direct_stencil<T>(op, mode, x, b, y, nrhs, omega_j, s);
   }
