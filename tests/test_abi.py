@@ -95,3 +95,11 @@ def test_joint_fit_matches_oracle(inv_g):
     assert np.max(np.abs(w7 - ref)) < 1e-7
     assert abs(w7[0] + w7[1] + w7[2] - 1) < 1e-14
     assert abs(w7[3] + 6 * w7[4] + 12 * w7[5] + 8 * w7[6] - 1) < 1e-14
+
+
+def test_context_setters_reject_a_null_context():
+    # hx_set_operator_form / hx_set_medium / hx_set_kernel_config touch no GPU
+    L = B.lib()
+    assert L.hx_set_operator_form(None, 1, 1) == -1
+    assert L.hx_set_medium(None, None, None) == -1
+    assert L.hx_set_kernel_config(None, 0) == -1
