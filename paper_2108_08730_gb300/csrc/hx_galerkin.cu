@@ -115,7 +115,7 @@ stored_stencil_k(const typename CT<T>::type* __restrict__ coef, int nx, int ny, 
 // coefficients formed on the fly (the same row as the tiled kernel) and the
 // neighbours read through the read-only cache.  A z-marching tiled kernel is
 // latency-bound when a level has only a few tiles.
-template <typename T, int MODE>
+template <typename T, int MODE, bool MED>
 __global__ void __launch_bounds__(128)
 direct_stencil_k(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
                  const typename CT<T>::type* __restrict__ b, typename CT<T>::type* __restrict__ y,
@@ -127,7 +127,7 @@ direct_stencil_k(OpDesc<T> op, const typename CT<T>::type* __restrict__ x,
        i += (long long)gridDim.x * blockDim.x) {
     const int ix = (int)(i % op.nx), iy = (int)((i / op.nx) % op.ny), iz = (int)(i / ((long long)op.nx * op.ny));
     C a[27];
-    fine_row<T>(op, ix, iy, iz, a);
+    fine_row<T, MED>(op, ix, iy, iz, a);
     const C dinv = cscale(omega_j, crcp(a[13]));
     for (int r = 0; r < R; ++r) {
       const long long o = (long long)r * N + i;
@@ -221,13 +221,18 @@ cudaError_t launch_direct_stencil(const OpDesc<T>& op, int mode, const void* x, 
   const long long N = (long long)op.nx * op.ny * op.nz;
   const unsigned g = blocks_for(N, 128, 152 * 32);
   const T om = (T)omega_j;
+  const bool med = op.buoy || op.invq;
+#define HX_DIRECT(M)                                                                                    \
+  (med ? launch_k(direct_stencil_k<T, M, true>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om) \
+       : launch_k(direct_stencil_k<T, M, false>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om))
   switch (mode) {
-    case kApply: (void)launch_k(direct_stencil_k<T, kApply>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om); break;
-    case kResidual: (void)launch_k(direct_stencil_k<T, kResidual>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om); break;
-    case kJacobi: (void)launch_k(direct_stencil_k<T, kJacobi>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om); break;
-    case kJacobi0: (void)launch_k(direct_stencil_k<T, kJacobi0>, g, 128, 0, s, op, (const C*)x, (const C*)b, (C*)y, R, om); break;
+    case kApply: (void)HX_DIRECT(kApply); break;
+    case kResidual: (void)HX_DIRECT(kResidual); break;
+    case kJacobi: (void)HX_DIRECT(kJacobi); break;
+    case kJacobi0: (void)HX_DIRECT(kJacobi0); break;
     default: return cudaErrorInvalidValue;
   }
+#undef HX_DIRECT
   count_launch(1);
   return cudaGetLastError();
 }

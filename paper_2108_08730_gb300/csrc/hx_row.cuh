@@ -40,8 +40,8 @@ __device__ __forceinline__ void table_row(const OpDesc<T>& op, T vt, T w[11]) {
 
 // fine_row with buoyancy and / or attenuation; w: the row's 11 table entries
 template <typename T>
-__device__ __noinline__ void medium_row(const OpDesc<T>& op, int ix, int iy, int iz, const T w[11],
-                                        typename CT<T>::type c[27]) {
+__device__ __forceinline__ void medium_row(const OpDesc<T>& op, int ix, int iy, int iz, const T w[11],
+                                           typename CT<T>::type c[27]) {
   using C = typename CT<T>::type;
   const long long sy = op.nx, sz = (long long)op.nx * op.ny;
   // b over the 3 x 3 x 3 block (0 outside the grid) and the in-grid flags
@@ -106,7 +106,9 @@ __device__ __noinline__ void medium_row(const OpDesc<T>& op, int ix, int iy, int
   }
 }
 
-template <typename T>
+// MED: the heterogeneous-medium row (op.buoy / op.invq set); a separate
+// instantiation, so the common kernels carry none of its code or state
+template <typename T, bool MED = false>
 __device__ __forceinline__ void fine_row(const OpDesc<T>& op, int ix, int iy, int iz,
                                          typename CT<T>::type c[27]) {
   using C = typename CT<T>::type;
@@ -136,7 +138,7 @@ __device__ __forceinline__ void fine_row(const OpDesc<T>& op, int ix, int iy, in
   const T iv = (T)1 / vt;
   const T m = op.omega2 * iv * iv;
   const T tw[3] = {w[8], w[9], w[10]};
-  if (op.buoy || op.invq) {
+  if constexpr (MED) {
     medium_row(op, ix, iy, iz, w, c);
     return;
   }

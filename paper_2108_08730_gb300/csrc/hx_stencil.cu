@@ -425,6 +425,7 @@ __global__ void jacobi0_kernel(OpDesc<T> op, const typename CT<T>::type* __restr
 
 // One thread per row: the 27 coefficients in (dk, dj, di) order, FP64
 // (entries whose neighbour lies outside the grid are 0).
+template <bool MED>
 __global__ void row_coef_kernel(OpDesc<double> op, double2* __restrict__ coef) {
   pdl_enter();
   const long long N = (long long)op.nx * op.ny * op.nz;
@@ -434,7 +435,7 @@ __global__ void row_coef_kernel(OpDesc<double> op, double2* __restrict__ coef) {
     const int iy = (int)((i / op.nx) % op.ny);
     const int iz = (int)(i / ((long long)op.nx * op.ny));
     double2 c[27];
-    fine_row<double>(op, ix, iy, iz, c);
+    fine_row<double, MED>(op, ix, iy, iz, c);
     for (int k = 0; k < 27; ++k) {
       const int di = k % 3 - 1, dj = (k / 3) % 3 - 1, dk = k / 9 - 1;
       const bool inside = ix + di >= 0 && ix + di < op.nx && iy + dj >= 0 && iy + dj < op.ny &&
@@ -555,7 +556,10 @@ cudaError_t launch_row_coefficients(const OpDesc<double>& op, double* coef, cuda
   const long long N = (long long)op.nx * op.ny * op.nz;
   long long blocks = (N + 255) / 256;
   if (blocks > 152 * 32) blocks = 152 * 32;
-  (void)launch_k(row_coef_kernel, (unsigned)blocks, 256, 0, s, op, (double2*)coef);
+  if (op.buoy || op.invq)
+    (void)launch_k(row_coef_kernel<true>, (unsigned)blocks, 256, 0, s, op, (double2*)coef);
+  else
+    (void)launch_k(row_coef_kernel<false>, (unsigned)blocks, 256, 0, s, op, (double2*)coef);
   count_launch(1);
   return cudaGetLastError();
 }
