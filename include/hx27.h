@@ -50,7 +50,10 @@ typedef enum {
   HX_ERR_NUMERIC = -4,        /* NaN/Inf or breakdown detected                  */
   HX_ERR_TIMEOUT = -5,        /* a bounded device wait ran out                  */
   HX_ERR_CUDA = -6,           /* a CUDA runtime call failed                     */
-  HX_ERR_STATE = -7           /* call order (e.g. no weight table set yet)      */
+  HX_ERR_STATE = -7,          /* call order (e.g. no weight table set yet)      */
+  HX_ERR_CANCELLED = -8       /* stopped by its cancel flag (hx_solve_opts.cancel,
+                                 hx_server_cancel); the best iterate so far is in
+                                 the output when the solve had started           */
 } hx_status;
 
 typedef struct hx_ctx hx_ctx;
@@ -370,6 +373,10 @@ typedef struct {
                             many seconds of solving and return
                             HX_ERR_NOT_CONVERGED with the best iterate (a
                             deadline for serving); 0 (default): no limit        */
+  const int* cancel;     /* non-NULL: a host int read (atomically) where the host
+                            synchronises anyway; once non-zero the solve stops
+                            with HX_ERR_CANCELLED and the best iterate.  Another
+                            thread may set it at any time.  NULL (default)     */
 } hx_solve_opts;
 
 typedef struct {
@@ -497,6 +504,8 @@ typedef struct {
   double busy_s;                   /* first submission -> last completion (s)     */
   double peak_committed;           /* peak bytes committed by admission           */
   int max_concurrent;              /* most requests on the GPU at once            */
+  int64_t cancelled;               /* requests ended by hx_server_cancel (also
+                                      counted in failed)                          */
 } hx_server_stats;
 
 /* Create the engine (starts the worker threads).  Errors: HX_ERR_ARG,
@@ -513,6 +522,14 @@ int hx_server_submit(hx_server* srv, const hx_request* req, int64_t* ticket);
 int hx_server_wait(hx_server* srv, int64_t ticket, double timeout_s, hx_request_result* res);
 /* Statistics since creation (or the last reset).  reset = 1 clears them. */
 int hx_server_get_stats(hx_server* srv, hx_server_stats* st, int reset);
+
+/* Cancel a submitted request.  A queued request is removed and completes at
+ * once with status HX_ERR_CANCELLED (its wavefield is not written); a running
+ * one stops at its solve's next convergence check (see hx_solve_opts.cancel)
+ * and completes with HX_ERR_CANCELLED, its best iterate written.  The result
+ * is still collected with hx_server_wait.  Errors: HX_ERR_ARG (unknown or
+ * already collected ticket), HX_ERR_STATE (already finished). */
+int hx_server_cancel(hx_server* srv, int64_t ticket);
 /* Finish the queued requests, stop the workers and free everything. */
 void hx_server_destroy(hx_server* srv);
 

@@ -17,7 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libhx27.so")
 
 HX_OK = 0
 STATUS = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_OOM", -3: "HX_ERR_NOT_CONVERGED",
-          -4: "HX_ERR_NUMERIC", -5: "HX_ERR_TIMEOUT", -6: "HX_ERR_CUDA", -7: "HX_ERR_STATE"}
+          -4: "HX_ERR_NUMERIC", -5: "HX_ERR_TIMEOUT", -6: "HX_ERR_CUDA", -7: "HX_ERR_STATE",
+          -8: "HX_ERR_CANCELLED"}
 
 # every symbol include/hx27.h declares (checked by tests/test_abi.py)
 EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_error",
@@ -27,7 +28,7 @@ EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_
            "hx_autotune", "hx_stencil_sweep", "hx_server_create", "hx_server_submit",
            "hx_server_wait", "hx_server_get_stats", "hx_server_destroy", "hx_apply_batched",
            "hx_fit_joint_weights", "hx_set_table_ex", "hx_set_operator_form",
-           "hx_set_medium")
+           "hx_set_medium", "hx_server_cancel")
 
 NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
 APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
@@ -62,7 +63,7 @@ class hx_solve_opts(C.Structure):
                 ("coarse_sweeps", C.c_int), ("omega_jacobi", C.c_double),
                 ("source_spread", C.c_int), ("initial_guess", C.c_int), ("check_every", C.c_int),
                 ("coarse_galerkin", C.c_int), ("pml_cap", C.c_double), ("use_graphs", C.c_int),
-                ("autotune", C.c_int), ("time_limit_s", C.c_double)]
+                ("autotune", C.c_int), ("time_limit_s", C.c_double), ("cancel", C.c_void_p)]
 
 
 class hx_solve_report(C.Structure):
@@ -99,7 +100,7 @@ class hx_server_stats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("max_ms", C.c_double),
                 ("point_rhs", C.c_double), ("busy_s", C.c_double), ("peak_committed", C.c_double),
-                ("max_concurrent", C.c_int)]
+                ("max_concurrent", C.c_int), ("cancelled", C.c_int64)]
 
 
 _lib = None
@@ -144,6 +145,7 @@ def lib():
     L.hx_server_submit.argtypes = [vp, C.POINTER(hx_request), C.POINTER(C.c_int64)]
     L.hx_server_wait.argtypes = [vp, C.c_int64, d, C.POINTER(hx_request_result)]
     L.hx_server_get_stats.argtypes = [vp, C.POINTER(hx_server_stats), i]
+    L.hx_server_cancel.argtypes = [vp, C.c_int64]
     L.hx_server_destroy.argtypes = [vp]
     L.hx_server_destroy.restype = None
     L.hx_profile.argtypes = [vp, i]
@@ -462,6 +464,12 @@ class Server:
         self._keep.pop(ticket, None)
         return {"status": r.status, "report": r.report.as_dict(), "queue_ms": r.queue_ms,
                 "run_ms": r.run_ms, "latency_ms": r.latency_ms, "worker": r.worker}
+
+    def cancel(self, ticket):
+        """hx_server_cancel: the request completes with HX_ERR_CANCELLED (-8)."""
+        st = lib().hx_server_cancel(self._h, int(ticket))
+        if st != HX_OK:
+            raise HxError(st, "hx_server_cancel failed")
 
     def stats(self, reset=False):
         s = hx_server_stats()

@@ -23,6 +23,7 @@
 #include <deque>
 #include <list>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <set>
 #include <thread>
@@ -47,6 +48,7 @@ struct Pending {
   hx_solve_opts opts;             // copied options
   double est;                     // admission estimate (bytes)
   Clock::time_point t_submit;
+  std::shared_ptr<int> cancel;    // the solve's cancel flag (hx_server_cancel)
 };
 
 struct Model {
@@ -95,12 +97,13 @@ struct hx_server {
   double model_bytes = 0;
   std::map<int64_t, hx_request_result> results;
   std::set<int64_t> outstanding;     // submitted and not yet waited for
+  std::map<int64_t, std::shared_ptr<int>> running_flags;   // cancel flags of running requests
   int64_t next_ticket = 0;
   bool stop = false;
 
   // statistics
   std::vector<double> lat_ms;
-  int64_t submitted = 0, completed = 0, failed = 0;
+  int64_t submitted = 0, completed = 0, failed = 0, cancelled = 0;
   double point_rhs = 0, peak_committed = 0;
   int running = 0, max_running = 0;
   bool have_first = false;
@@ -178,6 +181,7 @@ void hx_server::worker_main(int w) {
     }
     Pending p = std::move(queue.front());
     queue.pop_front();
+    running_flags[p.ticket] = p.cancel;
     W.busy = true;
     W.committed = p.est;
     const auto t_start = Clock::now();
@@ -225,7 +229,7 @@ void hx_server::worker_main(int w) {
       status = hx_solve(W.ctx, &g, vdev, p.src.data(), (int)p.src.size(), p.req.nrhs, W.wf, &p.opts, &rep,
                         W.stream);
       rep.status = status;
-      if (status == HX_OK || status == HX_ERR_NOT_CONVERGED) {
+      if (status == HX_OK || status == HX_ERR_NOT_CONVERGED || status == HX_ERR_CANCELLED) {
         cudaError_t e = cudaMemcpyAsync(p.req.wavefield_host, W.wf, wfb, cudaMemcpyDeviceToHost, W.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(W.stream);
         if (e != cudaSuccess) status = HX_ERR_CUDA;
@@ -235,6 +239,8 @@ void hx_server::worker_main(int w) {
 
     // ---- bookkeeping
     lk.lock();
+    running_flags.erase(p.ticket);
+    if (status == HX_ERR_CANCELLED) ++cancelled;
     if (vdev) {
       auto it = models.find(model_key(p.req));
       if (it != models.end()) {
@@ -333,6 +339,8 @@ int hx_server_submit(hx_server* srv, const hx_request* req, int64_t* ticket) {
   if (req->opts) p.opts = *req->opts;
   else hx_solve_default_opts(&p.opts);
   p.opts.autotune = 0;                          // results must not depend on timing
+  p.cancel = std::make_shared<int>(0);
+  p.opts.cancel = p.cancel.get();
   p.est = estimate_bytes(req->grid, req->nrhs, p.opts.mode);
   if (p.est + model_size(req->grid) > srv->budget) return HX_ERR_OOM;
   p.t_submit = Clock::now();
@@ -389,8 +397,9 @@ int hx_server_get_stats(hx_server* srv, hx_server_stats* st, int reset) {
   st->busy_s = srv->have_first && srv->completed ? ms_between(srv->t_first, srv->t_last) / 1e3 : 0.0;
   st->peak_committed = srv->peak_committed;
   st->max_concurrent = srv->max_running;
+  st->cancelled = srv->cancelled;
   if (reset) {
-    srv->submitted = srv->completed = srv->failed = 0;
+    srv->submitted = srv->completed = srv->failed = srv->cancelled = 0;
     srv->lat_ms.clear();
     srv->point_rhs = 0;
     srv->peak_committed = 0;
@@ -398,6 +407,35 @@ int hx_server_get_stats(hx_server* srv, hx_server_stats* st, int reset) {
     srv->have_first = false;
   }
   return HX_OK;
+}
+
+int hx_server_cancel(hx_server* srv, int64_t ticket) {
+  if (!srv) return HX_ERR_ARG;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (!srv->outstanding.count(ticket)) return HX_ERR_ARG;
+  if (srv->results.count(ticket)) return HX_ERR_STATE;
+  auto run = srv->running_flags.find(ticket);
+  if (run != srv->running_flags.end()) {
+    __atomic_store_n(run->second.get(), 1, __ATOMIC_RELAXED);   // seen at the next check
+    return HX_OK;
+  }
+  for (auto it = srv->queue.begin(); it != srv->queue.end(); ++it) {
+    if (it->ticket != ticket) continue;
+    hx_request_result r;
+    std::memset(&r, 0, sizeof(r));
+    r.status = HX_ERR_CANCELLED;
+    r.report.status = HX_ERR_CANCELLED;
+    r.queue_ms = r.latency_ms = ms_between(it->t_submit, Clock::now());
+    r.worker = -1;
+    srv->queue.erase(it);
+    srv->results[ticket] = r;
+    ++srv->failed;
+    ++srv->cancelled;
+    srv->cv_done.notify_all();
+    srv->cv_work.notify_all();                  // the next request may be admitted now
+    return HX_OK;
+  }
+  return HX_ERR_STATE;
 }
 
 void hx_server_destroy(hx_server* srv) {

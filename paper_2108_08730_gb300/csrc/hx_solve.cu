@@ -180,11 +180,14 @@ class Run {
       cudaStream_t st)
       : ctx(c), S(s), grid(g), v_fine(v0), opt(o), stream(st), t0(std::chrono::steady_clock::now()) {}
 
-  // opts.time_limit_s ran out (checked where the host synchronises anyway)
+  // opts.time_limit_s ran out or opts.cancel was set (checked where the host
+  // synchronises anyway)
   bool past_deadline() const {
-    return opt.time_limit_s > 0 &&
-           std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count() > opt.time_limit_s;
+    return cancelled() || (opt.time_limit_s > 0 && std::chrono::duration<double>(
+                                                       std::chrono::steady_clock::now() - t0)
+                                                           .count() > opt.time_limit_s);
   }
+  bool cancelled() const { return opt.cancel && __atomic_load_n(opt.cancel, __ATOMIC_RELAXED) != 0; }
 
   template <typename T>
   OpDesc<T> desc(int l, double beta) const {
@@ -457,6 +460,7 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->use_graphs = 1;
   o->autotune = 1;
   o->time_limit_s = 0.0;
+  o->cancel = nullptr;
 }
 
 namespace {
@@ -963,6 +967,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
     report->setup_ms = std::chrono::duration<double, std::milli>(t_setup - t_start).count();
     report->solve_ms = std::chrono::duration<double, std::milli>(t_end - t_setup).count();
   }
+  if (worst > opt.tol && run.cancelled()) return finish(fail(ctx, HX_ERR_CANCELLED, "cancelled"));
   if (worst > opt.tol) return finish(fail(ctx, HX_ERR_NOT_CONVERGED, "tolerance not reached"));
   return finish(HX_OK);
 }

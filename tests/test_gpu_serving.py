@@ -1,6 +1,6 @@
 """GPU tests of the serving engine (hx_server_*): continuous admission of
 solve requests on several worker slots, device-memory admission, resident
-models across frequencies, and results independent of the mix.
+models across frequencies, cancellation, and results independent of the mix.
 
 Every wavefield is also checked against its own equation: the oracle's
 assembled matrix (Eq. 3 rows, Eqs. 4-8, GA weights) applied on the CPU must
@@ -147,3 +147,42 @@ def test_bad_requests_are_refused(otable):
     r = srv.wait(srv.submit(g, v, [(5, 5, 5, 0, 1.0)], 1, o), timeout=60.0)
     assert r["status"] == 0
     srv.close()
+
+
+def test_cancel_queued_and_running_requests(otable):
+    # hx_server_cancel: a queued request completes at once as cancelled; a
+    # running one stops at its next convergence check (best iterate written);
+    # the request served after them matches its solo result
+    import time
+    reqs = _requests(3, 31)
+    outs = [np.zeros((r["nrhs"],) + r["v"].shape, dtype=np.complex128) for r in reqs]
+    srv = B.Server(otable[1], slots=1)
+    long_r = reqs[0]
+    t_long = srv.submit(long_r["grid"], long_r["v"], long_r["src"], long_r["nrhs"], outs[0],
+                        model_id=long_r["model_id"], tol=1e-30, max_outer=100000, time_limit_s=30.0)
+    t_q = srv.submit(reqs[1]["grid"], reqs[1]["v"], reqs[1]["src"], reqs[1]["nrhs"], outs[1],
+                     model_id=reqs[1]["model_id"])
+    t_ok = srv.submit(reqs[2]["grid"], reqs[2]["v"], reqs[2]["src"], reqs[2]["nrhs"], outs[2],
+                      model_id=reqs[2]["model_id"])
+    time.sleep(1.5)                                 # the long request is on the GPU by now
+    srv.cancel(t_q)
+    srv.cancel(t_long)
+    r_long = srv.wait(t_long, timeout=60.0)
+    r_q = srv.wait(t_q, timeout=60.0)
+    r_ok = srv.wait(t_ok, timeout=120.0)
+    st = srv.stats()
+    with pytest.raises(B.HxError) as e:             # already collected
+        srv.cancel(t_ok)
+    assert e.value.code == -1
+    srv.close()
+    assert r_long["status"] == -8 and r_long["worker"] == 0 and r_long["run_ms"] < 30000.0
+    assert np.isfinite(outs[0]).all() and np.abs(outs[0]).max() > 0     # best iterate written
+    assert r_q["status"] == -8 and r_q["worker"] == -1
+    assert not outs[1].any()                                            # never ran
+    assert r_ok["status"] == 0
+    assert st["cancelled"] == 2 and st["failed"] == 2 and st["completed"] == 1
+    solo_srv = B.Server(otable[1], slots=1)
+    solo, res = _run(solo_srv, reqs[2:], concurrent=False)
+    solo_srv.close()
+    assert res[0]["status"] == 0
+    assert np.linalg.norm(solo[0] - outs[2]) <= 1e-6 * np.linalg.norm(solo[0])
