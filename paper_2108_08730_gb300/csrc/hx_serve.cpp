@@ -32,6 +32,7 @@
 
 #include "hx_context.h"
 #include "hx_internal.h"
+#include "hx_trace.h"
 
 namespace {
 
@@ -226,6 +227,7 @@ void hx_server::worker_main(int w) {
       else status = HX_ERR_OOM;
     }
     if (status == HX_OK) {
+      hx::TraceRange trace_req("served request");
       status = hx_solve(W.ctx, &g, vdev, p.src.data(), (int)p.src.size(), p.req.nrhs, W.wf, &p.opts, &rep,
                         W.stream);
       rep.status = status;

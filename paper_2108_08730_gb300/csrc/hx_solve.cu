@@ -23,6 +23,7 @@
 #include "hx_context.h"
 #include "hx_galerkin.cuh"
 #include "hx_internal.h"
+#include "hx_trace.h"
 #include "hx_launch.cuh"
 #include "hx_vec.cuh"
 
@@ -621,6 +622,8 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
                         int nsrc, int nrhs, void* wavefield_dev, const hx_solve_opts* opts_in,
                         hx_solve_report* report, void* stream_v) {
   if (!ctx) return HX_ERR_ARG;
+  TraceRange trace_solve("hx_solve");
+  TraceRange trace_setup("hx_solve setup");
   auto t_start = std::chrono::steady_clock::now();
   hx_solve_opts opt;
   if (opts_in) opt = *opts_in; else hx_solve_default_opts(&opt);
@@ -867,6 +870,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       return finish(st);
   }
   auto t_setup = std::chrono::steady_clock::now();
+  trace_setup.end();
 
   S->graph_ready = false;   // kernel parameters may differ from the last call
   Run run(ctx, S, grid, v_dev, opt, stream);
@@ -934,6 +938,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
     outer = 1;
   } else {
     while (outer < opt.max_outer && worst > opt.tol && !run.past_deadline()) {
+      TraceRange trace_step("refinement step");
       // inner complex64 solve of A d = r / ||r||
       std::vector<double> sc(R);
       std::vector<int> act(R);
