@@ -1,4 +1,4 @@
-"""Oracle: analytic references of the first two benchmarks (Section 3.1-3.2).
+"""Oracle: analytic references of the first two benchmarks (Sections 3.2-3.3).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
 

@@ -45,7 +45,7 @@ with its own 1/kappa, i.e. the coefficient of neighbour j is
 (omega^2 / v_j^2) w_class(j) instead of (omega^2 / v_0^2) w_class(j).
 
 Heterogeneous density and attenuation (Eq. 2, Eqs. 1.1-1.4; the paper's
-benchmarks keep b = 1 and no attenuation): with buoyancy b = 1/rho
+benchmarks keep b = 1 and no attenuation, Section 3.1): with buoyancy b = 1/rho
 each stretched second difference becomes the conservative form
   [b(i+1/2)(p(i+1)-p(i))/xi(i+1/2) - b(i-1/2)(p(i)-p(i-1))/xi(i-1/2)] / (xi(i) h^2)
 on its own stencil line, b at a half node the mean of its two nodes (b at the

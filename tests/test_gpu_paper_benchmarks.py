@@ -1,4 +1,4 @@
-"""The paper's first two benchmarks at their full size (Section 3.1-3.2,
+"""The paper's first two benchmarks at their full size (Sections 3.2-3.3,
 Table 1): a 10 km x 20 km x 10 km medium at h = 50 m with a 16-node PML on
 every face (233 x 433 x 233 = 23.5 M unknowns), the source at (5 km, 2 km,
 5 km), scored with the paper's l1 measure (Eq. eqerror) against the
