@@ -7,7 +7,9 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
   same for the imaginary part, W a linear gain with distance from the source.
   The paper does not say which samples enter the sum nor the gain's origin;
   reading: all supplied samples, W = distance to the source in metres.
-  Parity unpinned beyond its definition (no worked example in the paper).
+  No worked example in the paper; pinned by properties of the definition
+  (tests/test_oracle_metrics.py): a field scaled by (1 - eps) scores 2 eps,
+  real and imaginary parts are scored apart, W matters up to a factor.
 """
 from __future__ import annotations
 
