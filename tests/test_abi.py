@@ -103,3 +103,26 @@ def test_context_setters_reject_a_null_context():
     assert L.hx_set_operator_form(None, 1, 1) == -1
     assert L.hx_set_medium(None, None, None) == -1
     assert L.hx_set_kernel_config(None, 0) == -1
+
+
+def test_header_is_plain_c():
+    # the boundary is a C ABI: the header must compile as C99 on its own,
+    # and a C program must be able to link against the library's symbols
+    import shutil
+    import subprocess
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "use.c")
+        with open(src, "w") as f:
+            f.write('#include "hx27.h"\n#include <stdio.h>\n'
+                    "int main(void) { hx_solve_opts o; hx_solve_default_opts(&o);\n"
+                    '  printf("%d %g\\n", o.max_iter, o.tol); return hx_last_error(0) == 0; }\n')
+        out = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                              src, "-o", os.path.join(d, "use"), "-L", os.path.dirname(B.LIB_PATH), "-lhx27",
+                              "-Wl,-rpath," + os.path.dirname(B.LIB_PATH)], capture_output=True, text=True)
+        assert out.returncode == 0, out.stderr
+        run = subprocess.run([os.path.join(d, "use")], capture_output=True, text=True, timeout=60)
+        assert run.returncode == 0 and len(run.stdout.split()) == 2, (run.stdout, run.stderr)
