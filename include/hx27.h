@@ -346,8 +346,10 @@ typedef struct {
   int max_iter;          /* BiCGStab iterations per inner solve (default 2000)    */
   double shift_beta;     /* complex shift of the preconditioner (default 1.0)    */
   int mg_levels;         /* multigrid levels incl. the fine grid; 0 = automatic   */
-  int nu_pre, nu_post;   /* damped-Jacobi sweeps before / after coarse correction */
-  int coarse_sweeps;     /* damped-Jacobi sweeps on the coarsest level            */
+  int nu_pre, nu_post;   /* damped-Jacobi sweeps before / after coarse correction
+                            (default 2, 2)                                        */
+  int coarse_sweeps;     /* damped-Jacobi sweeps on the coarsest level when it is
+                            not solved exactly (default 4)                        */
   double omega_jacobi;   /* Jacobi damping (default 0.6)                          */
   int source_spread;     /* 0: grid delta (default); 1: consistent-mass spread    */
   int initial_guess;     /* 1: wavefield_dev holds the starting iterate           */
