@@ -15,7 +15,14 @@ Also reported on the same JSON line:
                which the library brackets each launch with events (it replays
                CUDA graphs in the first, value pass);
   accuracy     relative L2 error of the mixed solution against the plain FP64
-               GPU solve, and that FP64 form's own throughput;
+               GPU solve, that FP64 form's own throughput and its dominant
+               kernel class's achieved bandwidth (FP64-ALU-bound);
+  gpu_launches this library's kernel launches inside the timed steps (graph
+               replays counted per kernel);
+  clocks       nvidia-smi SM clocks and throttle reasons sampled during the
+               timed steps;
+  serving      the serving leg: seeded requests with Poisson arrivals on the
+               serving engine, p50 / p99 latency and point*RHS/s;
   cpu_baseline the CPU oracle (banded LU, all host cores) on a bounded sample
                of the same workload: the 24^3 corner-free sub-grid around the
                source with the same model, PML and frequency.
