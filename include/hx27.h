@@ -486,7 +486,9 @@ typedef struct {
   int nsrc, nrhs;
   void* wavefield_host;     /* complex128 [nrhs][nz][ny][nx], written when the
                                request completes; must stay valid until then     */
-  const hx_solve_opts* opts;/* NULL = hx_solve_default_opts; copied at submission */
+  const hx_solve_opts* opts;/* NULL = hx_solve_default_opts; copied at submission;
+                               the server sets autotune = 0 and its own cancel
+                               flag (see hx_server_cancel)                        */
 } hx_request;
 
 typedef struct {
