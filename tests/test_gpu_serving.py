@@ -164,7 +164,11 @@ def test_cancel_queued_and_running_requests(otable):
                      model_id=reqs[1]["model_id"])
     t_ok = srv.submit(reqs[2]["grid"], reqs[2]["v"], reqs[2]["src"], reqs[2]["nrhs"], outs[2],
                       model_id=reqs[2]["model_id"])
-    time.sleep(1.5)                                 # the long request is on the GPU by now
+    t0 = time.time()
+    while srv.stats()["max_concurrent"] < 1:        # wait until the long request has started
+        assert time.time() - t0 < 60.0
+        time.sleep(0.05)
+    time.sleep(0.5)
     srv.cancel(t_q)
     srv.cancel(t_long)
     r_long = srv.wait(t_long, timeout=60.0)
