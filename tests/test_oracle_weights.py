@@ -168,3 +168,21 @@ def test_lookup_interpolates_linearly(table):
     mid = W.lookup(T, inv_g, 0.2505)
     assert np.allclose(mid, 0.5 * (T[250] + T[251]), rtol=0, atol=1e-15)
     assert np.allclose(W.lookup(T, inv_g, 0.9), T[-1])
+
+
+def test_adaptive_weights_beat_fixed_ones_at_every_g(table):
+    # Section 2.2 / the paper's central claim: weights picked by the local G
+    # keep the phase-velocity error at every G below that of the fixed G4 and
+    # Gm weights (max over the propagation angles, G from 4 to 30)
+    inv_g, T = table
+    th, ph = W.angle_grid()
+    g4 = W.expand_weights(W.fit_joint([0.25]))
+    gm = W.expand_weights(W.fit_joint([1 / 4, 1 / 6, 1 / 8, 1 / 10]))
+
+    def err(w7, G):
+        return np.max(np.abs(W.phase_velocity(1 / G, th, ph, w7) - 1))
+
+    for G in np.linspace(4.0, 30.0, 105):
+        ga = err(W.lookup(T, inv_g, 1 / G), G)
+        assert ga <= err(g4, G) and ga <= err(gm, G), G
+        assert ga < 1e-4
