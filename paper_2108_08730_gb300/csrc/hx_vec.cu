@@ -16,8 +16,6 @@ inline dim3 grid_for(long long N, int R, int per_thread = 4) {
   return dim3((unsigned)b, (unsigned)R);
 }
 
-__device__ __forceinline__ double2 to_d2(float2 a) { return make_double2(a.x, a.y); }
-__device__ __forceinline__ double2 to_d2(double2 a) { return a; }
 template <class C> __device__ __forceinline__ C from_d2(double2 a);
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) { return make_float2((float)a.x, (float)a.y); }
 template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { return a; }
