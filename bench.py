@@ -49,6 +49,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Mpoint*RHS/s to 1e-6 rel err (mixed vs FP64 GPU)"
 UNIT = "Mpoint*RHS/s"
+# Algorithmic FP64 flops of the complex128 stencil: per point*RHS the class-sum
+# row (26 neighbours into 4 class sums: 23 complex additions = 46 flops; 4
+# real-by-complex products = 8; 3 complex additions = 6) and the sweep's update
+# (b - A x and the scaled correction, about 8); per point the row formation
+# (1/v, the lerp of 11 table entries, the class coefficients: about 40).
+FP64_FLOPS_PER_POINT_RHS = 68
+FP64_FLOPS_PER_POINT = 40
 
 
 def _args():
@@ -79,6 +86,11 @@ def _args():
                         "shifted operator (beta = 1, omega = 0.6), as inside the solve")
     p.add_argument("--kernel-cfg", default="auto",
                    help="complex64 kernel configuration: auto, tune, all, or an id")
+    p.add_argument("--large", default="tectonic,sharp_contrast",
+                   help="comma-separated large batched workloads solved once each with all their "
+                        "sources (RHS split over the ranks) plus the stencil roofline at that size; "
+                        "'' skips the leg")
+    p.add_argument("--large-time-limit", type=float, default=300.0)
     return p.parse_args()
 
 
@@ -315,7 +327,7 @@ def run_gpu(args):
 
     # ---- end to end through the C ABI from pinned host buffers
     e2e_ms = []
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(max(1, args.steps)):
         flush.fill_(1.0)
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -329,6 +341,9 @@ def run_gpu(args):
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_total = reduce_max_ms(sum(e2e_ms), world, dev)
     e2e_value = aggregate_rate(units, world, len(e2e_ms), e2e_total)
+
+    # ---- large batched workloads (all ranks: each solves its slice of the RHS)
+    large = run_large(args, T, rank, world, local) if args.large else None
 
     if rank != 0:
         if world > 1:
@@ -359,10 +374,18 @@ def run_gpu(args):
             k64 = max(p64, key=lambda k: p64[k][1])
             n64, ms64, by64 = p64[k64]
             peak = (_peaks() or {}).get("hbm_gbs", 6800.0)
+            fp64_peak = ctx.fp64_peak()
+            flops = n64 * (FP64_FLOPS_PER_POINT_RHS * N * R + FP64_FLOPS_PER_POINT * N)
+            gflops = flops / (ms64 / 1e3) / 1e9
             roof64 = {"kernel": {"apply64": "stencil_kernel<double, kApply>",
                                  "smooth64": "stencil_kernel<double, kJacobi|kResidual>"}[k64],
-                      "achieved_gbs": round(by64 / (ms64 / 1e3) / 1e9, 1), "frac_of_hbm": round(by64 / (ms64 / 1e3) / 1e9 / peak, 4),
-                      "bound": "FP64 ALU (GB300 runs FP64 at a small fraction of its FP32 rate)"}
+                      "bound": "alu",
+                      "flops_per_point_rhs": FP64_FLOPS_PER_POINT_RHS, "flops_per_point": FP64_FLOPS_PER_POINT,
+                      "achieved_gflops": round(gflops, 1), "fp64_peak_gflops": round(fp64_peak, 1),
+                      "frac_of_fp64_peak": round(gflops / fp64_peak, 4),
+                      "fp64_peak_source": "hx_measure_fp64_peak (independent FMA chains, CUDA events, this run)",
+                      "achieved_gbs": round(by64 / (ms64 / 1e3) / 1e9, 1),
+                      "frac_of_hbm": round(by64 / (ms64 / 1e3) / 1e9 / peak, 4)}
         acc = {"rel_l2_mixed_vs_fp64": err, "fp64_status": rep64["status"],
                "fp64_rel_residual": rep64["rel_residual"], "fp64_iters": rep64["inner_iters"],
                "fp64_value": round(units / t64 / 1e6, 4), "fp64_unit": UNIT,
@@ -419,6 +442,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "cpu_baseline": cpu,
+        "large": large,
         "serving": serving,
     }
     print(json.dumps(line), flush=True)
@@ -426,6 +450,97 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_large(args, T, rank, world, local):
+    """The large batched workloads (tectonic 401x401x187 with 16 sources,
+    sharp contrast 201x201x101 with 64), each solved once in mixed precision
+    with all its sources as RHS (split over the ranks when world > 1): wall
+    time from the call to the wavefields on the device, the library's setup
+    (hierarchy, coarse inverse, autotune, first-call workspace) and solve
+    times apart, iterations, the FP64 relative residual the refinement
+    reached, and the clocks during the solve.  Then, at the same size, the
+    complex64 stencil's CUDA-event roofline: y = A x at 1, 4 and 16 RHS and
+    the damped-Jacobi sweep at 16 RHS, each autotuned, L2 flushed before every
+    timed launch, median of 5."""
+    import torch
+
+    from paper_2108_08730_gb300 import binding as B
+    from paper_2108_08730_gb300 import replicas as RP
+    from paper_2108_08730_gb300 import synth
+
+    dev = torch.device("cuda", local)
+    peaks = _peaks()
+    hbm = peaks["hbm_gbs"] if peaks else 6800.0
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for name in [w for w in args.large.split(",") if w]:
+        wl = synth.CONFIGS[name]()
+        ctx = B.Context(local, table=T)
+        g = B.grid_of(wl)
+        vd = torch.from_numpy(wl.v).to(dev)
+        N = wl.n_points
+        src, (lo, hi) = RP.local_sources(B.sources_of(wl), wl.nrhs, world, rank)
+        R = hi - lo
+        out = torch.zeros((R,) + wl.shape, dtype=torch.complex128, device=dev)
+        clocks = Clocks(local)
+        torch.cuda.synchronize(dev)
+        clocks.start()
+        t0 = time.perf_counter()
+        rep = ctx.solve(g, vd, src, R, out, check=False, time_limit_s=args.large_time_limit)
+        torch.cuda.synchronize(dev)
+        wall_ms = reduce_max_ms((time.perf_counter() - t0) * 1e3, world, dev)
+        clk = clocks.stop()
+        solve_ms = reduce_max_ms(rep["solve_ms"], world, dev)
+        del out
+        entry = {
+            "workload": f"{name} {wl.shape[2]}x{wl.shape[1]}x{wl.shape[0]}, h={wl.h:g} m, f={wl.f:g} Hz, "
+                        f"{wl.nrhs} sources",
+            "nrhs": wl.nrhs, "rhs_per_rank": R, "points": N, "status": rep["status"],
+            "value": round(N * wl.nrhs / (solve_ms / 1e3) / 1e6, 4), "unit": UNIT,
+            "value_incl_setup": round(N * wl.nrhs / (wall_ms / 1e3) / 1e6, 4),
+            "ms": round(wall_ms, 1), "setup_ms": round(rep["setup_ms"], 1), "solve_ms": round(solve_ms, 1),
+            "inner_iters": rep["inner_iters"], "outer_iters": rep["outer_iters"],
+            "mg_levels": rep["mg_levels"], "rel_residual": rep["rel_residual"], "clocks": clk,
+        }
+        # stencil roofline at this size (rank 0 only: one GPU's kernel)
+        if rank == 0:
+            roof = []
+            for mode, nr in (("apply", 1), ("apply", 4), ("apply", 16), ("jacobi", 16)):
+                x = torch.randn((nr,) + wl.shape, dtype=torch.complex64, device=dev)
+                y = torch.empty_like(x)
+                b = torch.randn_like(x) if mode == "jacobi" else None
+                ctx.autotune(g, vd, nr)
+
+                def launch():
+                    if mode == "apply":
+                        ctx.apply(g, vd, x, y)
+                    else:
+                        ctx.sweep(g, vd, "jacobi", x, b, y, shift_beta=1.0, omega=0.6)
+
+                for _ in range(2):
+                    launch()
+                ts = []
+                for _ in range(5):
+                    flush.fill_(1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    launch()
+                    e1.record()
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = statistics.median(ts)
+                algo = (16 if mode == "apply" else 24) * N * nr + 4 * N
+                roof.append({"mode": mode, "nrhs": nr, "ms": round(ms, 4), "algo_bytes": algo,
+                             "achieved": round(algo / ms / 1e6, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(algo / ms / 1e6 / hbm, 4)})
+                del x, y, b
+            entry["stencil_roofline"] = roof
+            entry["stencil_peak_source"] = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback"
+        ctx.close()
+        torch.cuda.empty_cache()
+        res[name] = entry
+    return res
 
 
 def run_serving(args, T, nreq=None, seed0=5000, log=None):
@@ -482,7 +597,9 @@ def run_serving(args, T, nreq=None, seed0=5000, log=None):
             "inner_iters_median": float(np.median(iters)), "inner_iters_max": int(max(iters)),
             "arrival_rate_per_s": round(rate, 4), "offered_load": 0.8,
             "solo_capacity_mpoint_rhs_s": round(solo / 1e6, 3),
-            "p50_ms": round(st["p50_ms"], 2), "p99_ms": round(st["p99_ms"], 2),
+            "p50_ms": round(st["p50_ms"], 2),
+            # a 99th percentile needs at least 100 completed requests
+            "p99_ms": round(st["p99_ms"], 2) if st["completed"] >= 100 else None,
             "latency": "submission to wavefield on the host, completed requests",
             "max_ms": round(st["max_ms"], 2),
             "value": round(st["point_rhs"] / st["busy_s"] / 1e6, 4) if st["busy_s"] > 0 else None,
@@ -591,8 +708,24 @@ def run_kernel(args):
                           "peak_gbs": peak, "frac": round(algo / ms / 1e6 / peak, 4)}), flush=True)
 
 
+def _relaunch_distributed(n):
+    """`python bench.py --gpus N` with N > 1 and no launcher: run this script
+    again under torch.distributed.run, one process per GPU (127.0.0.1
+    rendezvous), and return its exit code."""
+    import socket
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = _args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and args.impl == "hx":
+        sys.exit(_relaunch_distributed(args.gpus))
     if args.kernel:
         run_kernel(args)
     elif args.solve_config:

@@ -288,11 +288,16 @@ int hx_assemble_csr(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
  *   Same arguments, output and result as hx_assemble_csr, for grids of at
  *   most HX_NOALLOC_MAX_POINTS points (HX_ERR_ARG with a message otherwise).
  *   The first call on each device looks up the scratch array's device address
- *   (cudaGetSymbolAddress) while the context's device is current; make that
- *   first call before any stream capture.
- *   All calls share the one scratch array: calls whose device work may overlap
- *   (other host threads or streams) race and must be serialised by the caller.
- *   Synchronises `stream`. */
+ *   (cudaGetSymbolAddress) while the context's device is current, and later
+ *   calls reuse that address; make that first call before any stream
+ *   capture, and do not reset the device (cudaDeviceReset) between calls.
+ *   All calls share the one device scratch array and one host staging copy,
+ *   on every GPU: two calls whose work overlapped would race and return each
+ *   other's coefficients.  The library therefore holds a process-wide lock
+ *   for the whole call (upload, kernel, stream synchronisation, CSR fill), so
+ *   calls from any host threads or GPUs run one at a time.  The scratch keeps
+ *   the last call's contents; every entry a call reads is written by that
+ *   call first.  Synchronises `stream`. */
 int hx_assemble_csr_noalloc(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
                             double shift_beta, int64_t* rowptr, int32_t* col,
                             double* val, int64_t nnz_cap, int64_t* nnz_out, void* stream);
@@ -420,6 +425,16 @@ int hx_profile(hx_ctx* ctx, int enable);
  * class, also when timing is off), total_ms = bytes = 0. */
 int hx_profile_read(hx_ctx* ctx, int kind, int64_t* launches, double* total_ms,
                     double* algo_bytes);
+
+/* Measured FP64 fused-multiply-add throughput of the context's GPU, in
+ * GFLOP/s (2 flops per FMA).  The paper has no counterpart: this is the
+ * roofline of the complex128 kernels (the plain FP64 solve and the FP64
+ * residual of the mixed form), which run on the FP64 units and are bounded by
+ * their rate rather than by HBM.  Launches a short kernel of independent FMA
+ * chains (one warm-up launch, then the best of three, CUDA events on stream),
+ * allocates and frees an 8-byte-per-block sink, synchronises stream.
+ * Errors: HX_ERR_ARG (null gflops), HX_ERR_CUDA. */
+int hx_measure_fp64_peak(hx_ctx* ctx, double* gflops, void* stream);
 
 /* Solve [M + S] p = s (Eq. 3) for nrhs right-hand sides built from point
  * sources (Section 3.1), GA weights per row, with the given grid/PML.

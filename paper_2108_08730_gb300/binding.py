@@ -23,7 +23,7 @@ STATUS = {0: "HX_OK", -1: "HX_ERR_ARG", -2: "HX_ERR_OOM", -3: "HX_ERR_NOT_CONVER
 # every symbol include/hx27.h declares (checked by tests/test_abi.py)
 EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_error",
            "hx_set_table", "hx_apply_operator", "hx_row_coefficients", "hx_assemble_csr",
-           "hx_solve_default_opts", "hx_solve", "hx_profile", "hx_profile_read",
+           "hx_solve_default_opts", "hx_solve", "hx_profile", "hx_profile_read", "hx_measure_fp64_peak",
            "hx_assemble_csr_noalloc", "hx_kernel_config_info", "hx_set_kernel_config",
            "hx_autotune", "hx_stencil_sweep", "hx_server_create", "hx_server_submit",
            "hx_server_wait", "hx_server_get_stats", "hx_server_destroy", "hx_apply_batched",
@@ -137,6 +137,7 @@ def lib():
                            C.POINTER(hx_solve_opts), C.POINTER(hx_solve_report), vp]
     L.hx_assemble_csr_noalloc.argtypes = L.hx_assemble_csr.argtypes
     L.hx_stencil_sweep.argtypes = [vp, C.POINTER(hx_grid), vp, d, i, vp, vp, vp, i, i, d, vp]
+    L.hx_measure_fp64_peak.argtypes = [vp, dp, vp]
     L.hx_kernel_config_info.argtypes = [i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.hx_set_kernel_config.argtypes = [vp, i]
     L.hx_autotune.argtypes = [vp, C.POINTER(hx_grid), vp, i, i, C.POINTER(C.c_int), dp, i, vp]
@@ -385,6 +386,13 @@ class Context:
                         "hx_profile_read")
             out[name] = (n.value, ms.value, by.value)
         return out
+
+    def fp64_peak(self, stream=None):
+        """hx_measure_fp64_peak: measured FP64 FMA throughput in GFLOP/s."""
+        g = C.c_double(0)
+        self._check(lib().hx_measure_fp64_peak(self._h, C.byref(g), _stream_ptr(stream)),
+                    "hx_measure_fp64_peak")
+        return g.value
 
     def assemble_csr(self, grid, v, shift_beta=0.0, stream=None):
         """-> (rowptr int64, col int32, val complex128) numpy arrays."""

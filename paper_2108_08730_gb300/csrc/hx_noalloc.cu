@@ -14,9 +14,17 @@
 // cannot pass the arrays' names to a kernel (in host code they only stand in
 // for the symbols), so the first call on each device looks up their device
 // addresses with cudaGetSymbolAddress while that device is current, and
-// later calls reuse them.  All calls share the arrays: two calls whose device
-// work overlaps (other host threads, other streams) overwrite each other's
-// scratch and must be serialised by the caller.
+// later calls reuse them (which assumes the device's primary context is not
+// torn down and recreated, e.g. by cudaDeviceReset, while the process runs).
+//
+// All calls share the device arrays and one host staging copy of them.  Two
+// calls whose work overlapped -- on the same GPU or on different GPUs, from
+// any host threads or streams -- would overwrite each other's scratch and
+// return each other's coefficients, so every call holds one process-wide
+// lock from the first upload to the last read of the staging copy (the call
+// synchronises its stream before it lets go).  Calls are therefore
+// serialised; the lock does not cover other processes, which load their own
+// copy of the library and its arrays.
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -50,9 +58,9 @@ DeviceScratch g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
 // Device addresses of the scratch arrays on `device` (which must be current).
+// The caller holds g_scratch_mu.
 int scratch_for(hx_ctx* ctx, int device, DeviceScratch* out) {
   if (device < 0 || device >= kMaxDevices) return fail(ctx, HX_ERR_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
   DeviceScratch& s = g_scratch[device];
   if (!s.ready) {
     void* a = nullptr;
@@ -91,9 +99,18 @@ extern "C" int hx_assemble_csr_noalloc(hx_ctx* ctx, const hx_grid* grid, const f
                 "use hx_assemble_csr");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+  // held until the CSR is filled from the host staging copy (see the top of
+  // this file): no other call may touch the scratch or the staging meanwhile
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  cudaStream_t s = (cudaStream_t)stream;
+  // on every exit, error paths included, the work this call enqueued has
+  // finished before the lock is released (destroyed before `lock`)
+  struct Drain {
+    cudaStream_t s;
+    ~Drain() { cudaStreamSynchronize(s); }
+  } drain{s};
   DeviceScratch sc;
   if ((st = scratch_for(ctx, ctx->device, &sc))) return st;
-  cudaStream_t s = (cudaStream_t)stream;
 
   // per-axis PML coefficients 1/(xi(i) xi(i +- 1/2) h^2), same reading as the
   // operator (gamma0 (d/L)^2 damping, xi = 1 + i gamma/omega)
