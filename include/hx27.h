@@ -227,6 +227,23 @@ int hx_stencil_sweep(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doubl
                      int kind, const void* x_dev, const void* b_dev, void* y_dev, int nrhs,
                      int precision, double omega, void* stream);
 
+/* hx_apply_operator (kind 0) and hx_stencil_sweep (kind HX_SWEEP_RESIDUAL /
+ * HX_SWEEP_JACOBI), complex64 only, on fields whose x rows are padded to
+ * `pitch` elements: element (ix, iy, iz) of field r sits at
+ * r * pitch * ny * nz + (iz * ny + iy) * pitch + ix.  The paper has no
+ * counterpart: this is the layout hx_solve keeps its complex64 fields in
+ * (pitch = nx rounded up to a multiple of 4), exposed for callers that hold
+ * wavefields the same way.  An even pitch (16-byte rows) runs the kernel that
+ * moves each plane tile with one tensor-memory-access copy; pitch = nx (any
+ * nx) is the same as hx_apply_operator / hx_stencil_sweep.  Padding elements
+ * are neither read nor written.  x, b 16-byte aligned, y 8-byte aligned; b
+ * may be NULL for the residual (b = 0).  Asynchronous on stream.
+ * Errors: HX_ERR_ARG (pitch odd and != nx, or < nx; alignment), HX_ERR_STATE,
+ * HX_ERR_CUDA. */
+int hx_stencil_pitched(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, double shift_beta,
+                       int kind, const void* x_dev, const void* b_dev, void* y_dev, int nrhs,
+                       int64_t pitch, double omega, void* stream);
+
 /* One problem of hx_apply_batched: y = A x on its own grid and velocity. */
 typedef struct {
   hx_grid grid;
@@ -242,9 +259,12 @@ typedef struct {
  * is cut into items (problem, 32 x 8 column tile, z-chunk, block of RHS),
  * largest problems first; resident CTAs take items from a device counter
  * until none is left, so uneven sizes balance across the SMs.  Every output
- * equals hx_apply_operator's for the same kernel configuration (the
- * configuration is the context's forced one, else the default for the
- * smallest nrhs).  shift_beta as in hx_apply_operator, common to all.
+ * equals hx_apply_operator's for the same kernel configuration on grids
+ * where hx_apply_operator runs the same z-marching kernel (odd nx; with even
+ * nx it takes the tensor-copy kernel, whose results differ only in FP32
+ * rounding order).  The configuration is the context's forced one (ids 0-2),
+ * else the default for the smallest nrhs.  shift_beta as in
+ * hx_apply_operator, common to all.
  * The plan is staged through a pinned host buffer and a device buffer owned
  * by ctx, sized by the first call (later calls with no more work reuse them;
  * such calls can be recorded into a CUDA graph: a call made while the stream
@@ -304,16 +324,24 @@ int hx_assemble_csr_noalloc(hx_ctx* ctx, const hx_grid* grid, const float* v_dev
 
 /* ---------------------------------------------------------------- tuning */
 
-/* The complex64 operator kernel (used by hx_apply_operator with precision 32
- * and by every complex64 stencil sweep of hx_solve on grids above the
- * direct-kernel size) exists in several launch configurations: tile rows per
- * thread x right-hand sides per CTA.  All compute the same operator (results
- * differ only in FP32 rounding order); their speed depends on the grid and
- * nrhs.  The paper has no counterpart (its solver is a sparse direct
- * factorisation); this only chooses between launch shapes.
- * hx_kernel_config_info returns the number of configurations and, for a
- * valid cfg, writes its rows per thread and RHS per CTA (either pointer may
- * be NULL).  Needs no context. */
+/* The complex64 operator (hx_apply_operator with precision 32,
+ * hx_stencil_sweep, hx_stencil_pitched and every complex64 stencil sweep of
+ * hx_solve on grids above the direct-kernel size) runs on one of two
+ * z-marching kernels, each in several launch configurations:
+ *   ids 0-2: fields whose rows are not 16-byte aligned (odd nx, pitch = nx);
+ *            per-thread asynchronous copies; 1, 2, 4 RHS per CTA;
+ *   ids 3-8: rows of even pitch (the layout hx_solve uses); one
+ *            tensor-memory-access copy per plane tile, the x/y-PML rows in a
+ *            separate kernel; (8 rows, 1 / 2 / 4 / 8 RHS) and (16 rows,
+ *            2 / 4 RHS) per CTA.
+ * All compute the same operator (results differ only in FP32 rounding
+ * order); their speed depends on the grid and nrhs.  A configuration that
+ * does not serve a launch's layout is replaced by the automatic choice.  The
+ * paper has no counterpart (its solver is a sparse direct factorisation);
+ * this only chooses between launch shapes.  hx_kernel_config_info returns
+ * the number of configurations and, for a valid cfg, writes its rows per
+ * thread (1 for all) and RHS per CTA (either pointer may be NULL).  Needs no
+ * context. */
 int hx_kernel_config_info(int cfg, int* rows_per_thread, int* rhs_per_cta);
 
 /* Force configuration cfg for every later complex64 launch on ctx; cfg = -1
@@ -321,13 +349,16 @@ int hx_kernel_config_info(int cfg, int* rows_per_thread, int* rhs_per_cta);
  * launch's grid size and nrhs, else a default by nrhs).  Errors: HX_ERR_ARG. */
 int hx_set_kernel_config(hx_ctx* ctx, int cfg);
 
-/* Time every configuration of the complex64 apply (shifted form, nrhs
- * fields, one warm-up then ncalls launches each, CUDA events on stream) on
- * this grid and velocity, and record the fastest for (nx, ny, nz, nrhs) in
- * ctx; later hx_apply_operator / hx_solve launches of that size use it.
+/* Time every configuration of the complex64 apply that serves this grid's
+ * own layout (pitch = nx: ids 3-8 for even nx, 0-2 for odd nx; shifted form,
+ * nrhs fields, one warm-up then ncalls launches each, CUDA events on stream;
+ * configurations with at least twice nrhs RHS per CTA are skipped) on this
+ * grid and velocity, and record the fastest for (nx, ny, nz, nrhs) in ctx;
+ * later hx_apply_operator / hx_solve launches of that size use it (hx_solve
+ * tunes its own padded layout itself when this size has no entry).
  *   best_cfg: receives the chosen configuration (may be NULL);
  *   ms_out:   receives up to ms_cap per-launch times in ms, by configuration
- *             (may be NULL).
+ *             id (1e300 for configurations not timed; may be NULL).
  * Allocates two temporary complex64 fields (nrhs * N each) and frees them;
  * synchronises stream; refuses to run while stream is being captured
  * (HX_ERR_STATE).  Errors: HX_ERR_ARG, HX_ERR_STATE, HX_ERR_OOM, HX_ERR_CUDA. */

@@ -28,7 +28,7 @@ EXPORTS = ("hx_build_weight_table", "hx_ctx_create", "hx_ctx_destroy", "hx_last_
            "hx_autotune", "hx_stencil_sweep", "hx_server_create", "hx_server_submit",
            "hx_server_wait", "hx_server_get_stats", "hx_server_destroy", "hx_apply_batched",
            "hx_fit_joint_weights", "hx_set_table_ex", "hx_set_operator_form",
-           "hx_set_medium", "hx_server_cancel")
+           "hx_set_medium", "hx_server_cancel", "hx_stencil_pitched")
 
 NOALLOC_MAX_POINTS = 19683     # HX_NOALLOC_MAX_POINTS in include/hx27.h
 APPLY_DIRECT = 0x100           # HX_APPLY_DIRECT in include/hx27.h
@@ -138,6 +138,7 @@ def lib():
     L.hx_assemble_csr_noalloc.argtypes = L.hx_assemble_csr.argtypes
     L.hx_stencil_sweep.argtypes = [vp, C.POINTER(hx_grid), vp, d, i, vp, vp, vp, i, i, d, vp]
     L.hx_measure_fp64_peak.argtypes = [vp, dp, vp]
+    L.hx_stencil_pitched.argtypes = [vp, C.POINTER(hx_grid), vp, d, i, vp, vp, vp, i, C.c_int64, d, vp]
     L.hx_kernel_config_info.argtypes = [i, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.hx_set_kernel_config.argtypes = [vp, i]
     L.hx_autotune.argtypes = [vp, C.POINTER(hx_grid), vp, i, i, C.POINTER(C.c_int), dp, i, vp]
@@ -386,6 +387,18 @@ class Context:
                         "hx_profile_read")
             out[name] = (n.value, ms.value, by.value)
         return out
+
+    def stencil_pitched(self, grid, v, kind, x, b, y, pitch, shift_beta=0.0, omega=0.6, stream=None):
+        """hx_stencil_pitched on complex64 torch CUDA tensors (nrhs, nz, ny,
+        pitch); kind "apply", "residual" or "jacobi"; b may be None for apply
+        and residual."""
+        k = {"apply": 0, "residual": 1, "jacobi": 2}[kind]
+        nrhs = x.shape[0]
+        bp = C.c_void_p(b.data_ptr()) if b is not None else None
+        self._check(lib().hx_stencil_pitched(self._h, C.byref(grid), C.c_void_p(v.data_ptr()),
+                                             float(shift_beta), k, C.c_void_p(x.data_ptr()), bp,
+                                             C.c_void_p(y.data_ptr()), nrhs, int(pitch), float(omega),
+                                             _stream_ptr(stream)), "hx_stencil_pitched")
 
     def fp64_peak(self, stream=None):
         """hx_measure_fp64_peak: measured FP64 FMA throughput in GFLOP/s."""

@@ -458,6 +458,37 @@ int hx_stencil_sweep(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doubl
   return HX_OK;
 }
 
+int hx_stencil_pitched(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, double shift_beta, int kind,
+                       const void* x_dev, const void* b_dev, void* y_dev, int nrhs, int64_t pitch, double omega,
+                       void* stream) {
+  if (!ctx) return HX_ERR_ARG;
+  int st = check_grid(ctx, grid);
+  if (st) return st;
+  if (!ctx->tab64) return fail(ctx, HX_ERR_STATE, "no weight table set (hx_set_table)");
+  if (kind != 0 && kind != HX_SWEEP_RESIDUAL && kind != HX_SWEEP_JACOBI)
+    return fail(ctx, HX_ERR_ARG, "unknown kind (0 = apply, HX_SWEEP_RESIDUAL, HX_SWEEP_JACOBI)");
+  if (!v_dev || !x_dev || !y_dev || nrhs < 1 || (kind == HX_SWEEP_JACOBI && !b_dev))
+    return fail(ctx, HX_ERR_ARG, "null buffer or nrhs < 1");
+  if (x_dev == y_dev || (b_dev && b_dev == y_dev)) return fail(ctx, HX_ERR_ARG, "y must overlap neither x nor b");
+  if (pitch < grid->nx || (pitch != grid->nx && (pitch & 1)))
+    return fail(ctx, HX_ERR_ARG, "pitch must be nx or an even number >= nx");
+  if (((uintptr_t)x_dev & 15) || ((uintptr_t)b_dev & 15) || ((uintptr_t)y_dev & 7))
+    return fail(ctx, HX_ERR_ARG, "x and b must be 16-byte aligned, y 8-byte aligned");
+  if (!std::isfinite(shift_beta) || !std::isfinite(omega)) return fail(ctx, HX_ERR_ARG, "non-finite parameter");
+  cudaSetDevice(ctx->device);
+  Level* lv = nullptr;
+  const int nl[3] = {grid->nx, grid->ny, grid->nz};
+  if ((st = get_level(ctx, grid, nl, grid->h, &lv))) return st;
+  const int mode = kind == 0 ? kApply : (kind == HX_SWEEP_RESIDUAL ? kResidual : kJacobi);
+  OpDesc<float> d = make_desc<float>(ctx, *lv, v_dev, shift_beta);
+  d.cfg32 = ctx_cfg32(ctx, grid->nx, grid->ny, grid->nz, nrhs);
+  d.pitch = pitch;
+  const cudaError_t e = launch_stencil(d, mode, x_dev, kind == 0 ? nullptr : b_dev, y_dev, nrhs,
+                                       (long long)pitch * grid->ny * grid->nz, omega, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "stencil launch");
+  return HX_OK;
+}
+
 int hx_apply_batched(hx_ctx* ctx, const hx_apply_item* items, int n, double shift_beta, void* stream) {
   if (!ctx) return HX_ERR_ARG;
   if (!items || n < 1 || n > (1 << 20)) return fail(ctx, HX_ERR_ARG, "need 1 <= n <= 2^20 items");

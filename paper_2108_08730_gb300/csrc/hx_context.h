@@ -103,7 +103,7 @@ int ctx_cfg32(const hx_ctx* ctx, int nx, int ny, int nz, int nrhs);
 // autotuner core (hx_tune.cu): times the configurations on level lv with
 // caller-owned buffers and records the fastest for (level size, nrhs)
 int tune_cfg32(hx_ctx* ctx, const Level& lv, const float* v_dev, int nrhs, const void* x, void* y,
-               int ncalls, cudaStream_t s, int* best_cfg, double* ms_out, int ms_cap);
+               long long pitch, int ncalls, cudaStream_t s, int* best_cfg, double* ms_out, int ms_cap);
 int cuda_fail(hx_ctx* ctx, cudaError_t e, const char* where);
 int check_grid(hx_ctx* ctx, const hx_grid* g);
 // Level for grid g evaluated at spacing h_level with n_level nodes per axis

@@ -50,6 +50,10 @@ struct OpDesc {
   // grid, or null (b = 1, no attenuation); set only on the operator itself
   const float* buoy = nullptr;
   const float* invq = nullptr;
+  // x-row pitch (elements) of the complex fields this descriptor is launched
+  // on; 0 = nx (fields back to back).  An even pitch (16-byte rows) selects
+  // the TMA complex64 kernel (hx_zmarch.cu).
+  long long pitch = 0;
 };
 
 enum StencilMode { kApply = 0, kResidual = 1, kJacobi = 2, kJacobi0 = 3 };
@@ -95,6 +99,19 @@ cudaError_t launch_stencil32_group(int cfg, const GroupProb* probs_dev, const Gr
                                    int* counter_dev, cudaStream_t s);
 
 cudaError_t launch_row_coefficients(const OpDesc<double>& op, double* coef, cudaStream_t s);
+
+// Complex64 launch configurations visible through the C ABI: ids 0..2 are the
+// cp.async z-marching kernel (any nx; RHS per CTA 1, 2, 4), ids 3.. the TMA
+// kernel (even row pitch; hx_zmarch.cu's list shifted by kZmCfgBase).
+constexpr int kZmCfgBase = 3;
+int cfg32_count();
+// Row pitch a descriptor's fields use (op.pitch, or nx).
+template <typename T>
+inline long long field_pitch(const OpDesc<T>& op) { return op.pitch > 0 ? op.pitch : op.nx; }
+// Device flag set by a TMA-kernel CTA whose bounded wait ran out (read and
+// cleared by zm_take_error; 0 when none).
+int zm_take_error(int device);
+int* zm_error_flag(int device);
 
 // Kernels launched by the library in this process (every launcher counts).
 long long launch_count();

@@ -55,6 +55,10 @@ struct SolverImpl : Solver {
   int nlev = 0;
   int n[kMaxLev][3];
   long long N[kMaxLev];
+  // fine-level Krylov / multigrid fields of the inner precision: x-row pitch
+  // (complex64: nx rounded up to 4, so rows are 32-byte aligned and the TMA
+  // kernel loads plane tiles; complex128: nx) and elements per field
+  long long pitch0 = 0, NP = 0;
   std::string op_key;
   std::unique_ptr<Level> lvl[kMaxLev];  // preconditioner levels (capped PML)
   std::unique_ptr<Level> lvlA;          // the true fine-level operator
@@ -62,7 +66,7 @@ struct SolverImpl : Solver {
   DevBuf mb[kMaxLev], me[kMaxLev], mw[kMaxLev];
   DevBuf acoef[kMaxLev];                // Galerkin coarse operators [27][N_l] (level >= 1)
   bool galerkin = false;
-  // Krylov vectors (inner precision), R * N[0] complex each
+  // Krylov vectors (inner precision), R * NP complex each (padding kept zero)
   DevBuf r, rhat, p, v, s, t, x, ph, sh, tmp;
   DevBuf r64;                           // FP64 residual (mixed mode)
   DevBuf sc;                            // per-RHS scalars
@@ -194,6 +198,7 @@ class Run {
   OpDesc<T> desc(int l, double beta) const {
     OpDesc<T> d = make_desc<T>(ctx, *S->lvl[l], l == 0 ? v_fine : (const float*)S->vlev[l].p, beta, true);
     d.cfg32 = ctx_cfg32(ctx, S->n[l][0], S->n[l][1], S->n[l][2], S->R);
+    if (l == 0) d.pitch = S->pitch0;
     return d;
   }
 
@@ -209,7 +214,7 @@ class Run {
       return launch_direct_stencil<T>(op, mode, x, b, y, S->R, om, stream);
     const bool timed = l == 0 && mode != kJacobi0;
     cudaEvent_t a = timed ? prof_begin(ctx, stream) : nullptr;
-    cudaError_t e = launch_stencil(op, mode, x, b, y, S->R, N, om, stream);
+    cudaError_t e = launch_stencil(op, mode, x, b, y, S->R, l == 0 ? S->NP : N, om, stream);
     if (timed) {
       const int kind = mode == kApply ? (sizeof(T) == 4 ? HX_PROF_APPLY32 : HX_PROF_APPLY64)
                                       : (sizeof(T) == 4 ? HX_PROF_SMOOTH32 : HX_PROF_SMOOTH64);
@@ -245,10 +250,10 @@ class Run {
     }
     if (!coarsest) {
       HX_CK(stencil<T>(l, op, kResidual, cur, b, oth, 0.0));
-      HX_CK(launch_restrict<T>(oth, S->n[l], S->mb[l + 1].p, S->n[l + 1], R, stream));
+      HX_CK(launch_restrict<T>(oth, S->n[l], S->mb[l + 1].p, S->n[l + 1], R, stream, l == 0 ? S->pitch0 : 0));
       int st = vcycle<T>(l + 1, S->mb[l + 1].p, S->me[l + 1].p, S->mw[l + 1].p);
       if (st) return st;
-      HX_CK(launch_prolong_add<T>(cur, S->n[l], S->me[l + 1].p, S->n[l + 1], R, stream));
+      HX_CK(launch_prolong_add<T>(cur, S->n[l], S->me[l + 1].p, S->n[l + 1], R, stream, l == 0 ? S->pitch0 : 0));
       for (int k = 0; k < opt.nu_post; ++k) {
         HX_CK(stencil<T>(l, op, kJacobi, cur, b, oth, opt.omega_jacobi));
         std::swap(cur, oth);
@@ -263,7 +268,7 @@ class Run {
   template <typename T>
   int bicg_iteration(const OpDesc<T>& A) {
     const int R = S->R;
-    const long long N = S->N[0];
+    const long long N = S->NP;
     double2* part = (double2*)S->part.p;
     const BicgScalars sc = S->scalars();
     HX_CK(launch_bicg_p<T>(S->p.p, S->r.p, S->v.p, S->beta, S->omega, N, R, stream));
@@ -363,10 +368,11 @@ class Run {
   template <typename T>
   int bicgstab(double tol, int max_iter, const std::vector<int>& active_in, int* iters) {
     const int R = S->R;
-    const long long N = S->N[0];
+    const long long N = S->NP;
     const size_t fb = (size_t)R * N * 2 * sizeof(T);
     OpDesc<T> A = make_desc<T>(ctx, *S->lvlA, v_fine, 0.0);   // the true operator
     A.cfg32 = ctx_cfg32(ctx, S->n[0][0], S->n[0][1], S->n[0][2], R);
+    A.pitch = S->pitch0;
     void* r = S->r.p;
     void* rhat = S->rhat.p;
     void* p = S->p.p;
@@ -714,11 +720,16 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
         S->N[l] = (long long)lv_n[l][0] * lv_n[l][1] * lv_n[l][2];
       }
       const size_t cs = prec == 64 ? 16 : 8;
-      const size_t fb = (size_t)nrhs * S->N[0] * cs;
+      S->pitch0 = prec == 64 ? grid->nx : (grid->nx + 3) / 4 * 4;
+      S->NP = S->pitch0 * grid->ny * grid->nz;
+      const size_t fb = (size_t)nrhs * S->NP * cs;
       cudaError_t e = cudaSuccess;
       DevBuf* vecs[] = {&S->r, &S->rhat, &S->p, &S->v, &S->s, &S->t, &S->x, &S->ph, &S->sh, &S->tmp};
-      for (DevBuf* b : vecs)
+      for (DevBuf* b : vecs) {
         if (e == cudaSuccess) e = b->alloc(fb);
+        // the row padding is read as zeros by the vector kernels and never written
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->p, 0, fb, stream);
+      }
       if (e == cudaSuccess) e = S->r64.alloc((size_t)nrhs * S->N[0] * 16);
       for (int l = 1; l < nlev && e == cudaSuccess; ++l) {
         const size_t lb = (size_t)nrhs * S->N[l] * cs;
@@ -728,7 +739,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
         if (e == cudaSuccess) e = S->mw[l].alloc(lb);
       }
       if (e == cudaSuccess) e = S->sc.alloc((size_t)nrhs * (7 * 16 + 4 * 8 + 3 * 4) + 64);
-      if (e == cudaSuccess) e = S->part.alloc((size_t)2 * nrhs * reduce_blocks(S->N[0]) * 16);
+      if (e == cudaSuccess) e = S->part.alloc((size_t)2 * nrhs * reduce_blocks(std::max(S->N[0], S->NP)) * 16);
       if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "solver workspace"));
       char* q = (char*)S->sc.p;
       auto take = [&](size_t bytes) { char* r = q; q += bytes; return r; };
@@ -864,9 +875,9 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   // size and nrhs (the Krylov buffers serve as scratch before the solve)
   if (prec == 32 && opt.autotune && (long long)N * nrhs >= (1LL << 20) &&
       ctx->st32_cfg < 0 && !ctx->tuned.count(tune_key(grid->nx, grid->ny, grid->nz, nrhs))) {
-    if ((e = cudaMemsetAsync(S->p.p, 0, (size_t)nrhs * N * 8, stream)))
+    if ((e = cudaMemsetAsync(S->p.p, 0, (size_t)nrhs * S->NP * 8, stream)))
       return finish(cuda_fail(ctx, e, "autotune scratch"));
-    if ((st = tune_cfg32(ctx, *S->lvlA, v_dev, nrhs, S->p.p, S->v.p, 2, stream, nullptr, nullptr, 0)))
+    if ((st = tune_cfg32(ctx, *S->lvlA, v_dev, nrhs, S->p.p, S->v.p, S->pitch0, 2, stream, nullptr, nullptr, 0)))
       return finish(st);
   }
   auto t_setup = std::chrono::steady_clock::now();
@@ -948,14 +959,14 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
         sc[k] = a ? 1.0 / std::sqrt(rn2[k]) : 0.0;
       }
       if ((e = cudaMemcpyAsync(S->scale, sc.data(), R * sizeof(double), cudaMemcpyHostToDevice, stream)) ||
-          (e = launch_cast_scale(r64, (float2*)S->r.p, S->scale, N, R, stream)))
+          (e = launch_cast_scale(r64, (float2*)S->r.p, S->scale, N, R, stream, grid->nx, S->pitch0)))
         return finish(cuda_fail(ctx, e, "cast"));
       int its = 0;
       if ((st = run.bicgstab<float>(opt.inner_tol, opt.max_iter, act, &its))) return finish(st);
       inner_total += its;
       for (int k = 0; k < R; ++k) sc[k] = act[k] ? std::sqrt(rn2[k]) : 0.0;
       if ((e = cudaMemcpyAsync(S->scale, sc.data(), R * sizeof(double), cudaMemcpyHostToDevice, stream)) ||
-          (e = launch_axpy_mixed(x64, (const float2*)S->x.p, S->scale, N, R, stream)))
+          (e = launch_axpy_mixed(x64, (const float2*)S->x.p, S->scale, N, R, stream, grid->nx, S->pitch0)))
         return finish(cuda_fail(ctx, e, "update"));
       ++outer;
       if ((st = residual(false))) return finish(st);
@@ -964,6 +975,11 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   }
   prof_collect(ctx);
   auto t_end = std::chrono::steady_clock::now();
+  // a TMA-kernel CTA whose bounded wait for a plane ran out
+  if (zm_take_error(ctx->device)) {
+    if (report) report->rel_residual = worst;
+    return finish(fail(ctx, HX_ERR_TIMEOUT, "a stencil kernel's bounded wait for its plane copies ran out"));
+  }
   if (report) {
     report->outer_iters = outer;
     report->inner_iters = inner_total;

@@ -30,6 +30,7 @@
 #include "hx_galerkin.cuh"
 #include "hx_launch.cuh"
 #include "hx_row.cuh"
+#include "hx_zmarch.cuh"
 
 namespace hx {
 namespace {
@@ -532,9 +533,20 @@ cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const v
     if (rstride != (long long)op.nx * op.ny * op.nz) return cudaErrorInvalidValue;
     return launch_direct_stencil<T>(op, mode, x, b, y, nrhs, omega_j, s);
   }
+  // complex64 fields with 16-byte rows: the TMA z-marching kernel
+  if (sizeof(T) == 4 && (field_pitch(op) & 1) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)b & 15) == 0) {
+    const OpDesc<float>& of = reinterpret_cast<const OpDesc<float>&>(op);
+    const long long pitch = field_pitch(op);
+    if (rstride != pitch * op.ny * op.nz) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int zc = op.cfg32 >= kZmCfgBase ? op.cfg32 - kZmCfgBase : -1;
+    return launch_zmarch(of, mode, zc, x, b, y, nrhs, pitch, omega_j, zm_error_flag(dev), s);
+  }
+  if (op.pitch > 0 && op.pitch != op.nx) return cudaErrorInvalidValue;   // odd pitch: not supported
   // the complex64 kernel's bulk row copies need a 16-byte aligned x
   if (sizeof(T) == 4 && mode != kJacobi0 && ((uintptr_t)x & 15) == 0) {
-    const int cfg = op.cfg32 >= 0 && op.cfg32 < st32_num_configs() ? op.cfg32 : st32_default_config(nrhs);
+    const int cfg = op.cfg32 >= 0 && op.cfg32 < kZmCfgBase ? op.cfg32 : st32_default_config(nrhs);
     return launch_stencil32(reinterpret_cast<const OpDesc<float>&>(op), mode, cfg, x, b, y, nrhs,
                             rstride, omega_j, s);
   }

@@ -1,5 +1,5 @@
 // Autotuner of the complex64 operator kernel: times every configuration
-// (rows per thread x RHS per CTA) of the z-marching kernel on a grid and
+// (RHS per CTA, rows per CTA) of the z-marching kernel serving the layout and
 // records the fastest per (grid size, nrhs) in the context; launches on that
 // context then use it.  Not part of the paper's method (its solver is a
 // sparse direct factorisation); it only chooses between launch shapes that
@@ -10,6 +10,7 @@
 
 #include "hx_context.h"
 #include "hx_internal.h"
+#include "hx_zmarch.cuh"
 
 namespace hx {
 
@@ -24,58 +25,67 @@ int ctx_cfg32(const hx_ctx* ctx, int nx, int ny, int nz, int nrhs) {
 using namespace hx;
 
 namespace {
-// rows per thread and RHS per CTA of each configuration (hx_stencil32.cu)
-const int kCfgRows[] = {1, 1, 1};
-const int kCfgRhs[] = {1, 2, 4};
+// RHS per CTA of a configuration: ids < kZmCfgBase are the cp.async kernel
+// (hx_stencil32.cu), the others the TMA kernel (hx_zmarch.cu)
+int cfg_rhs(int cfg) { return cfg < kZmCfgBase ? st32_config_rhs(cfg) : zm_config(cfg - kZmCfgBase).rb; }
 }  // namespace
 
 extern "C" int hx_kernel_config_info(int cfg, int* rows_per_thread, int* rhs_per_cta) {
-  const int n = st32_num_configs();
+  const int n = cfg32_count();
   if (cfg >= 0 && cfg < n) {
-    if (rows_per_thread) *rows_per_thread = kCfgRows[cfg];
-    if (rhs_per_cta) *rhs_per_cta = kCfgRhs[cfg];
+    if (rows_per_thread) *rows_per_thread = 1;
+    if (rhs_per_cta) *rhs_per_cta = cfg_rhs(cfg);
   }
   return n;
 }
 
 extern "C" int hx_set_kernel_config(hx_ctx* ctx, int cfg) {
   if (!ctx) return HX_ERR_ARG;
-  if (cfg < -1 || cfg >= st32_num_configs()) return fail(ctx, HX_ERR_ARG, "unknown kernel configuration");
+  if (cfg < -1 || cfg >= cfg32_count()) return fail(ctx, HX_ERR_ARG, "unknown kernel configuration");
   ctx->st32_cfg = cfg;
   return HX_OK;
 }
 
 namespace hx {
 
-// Times every configuration of the complex64 apply on level lv with buffers
-// x, y (nrhs fields of the level's size, caller-owned) and records the
-// fastest in ctx.  Synchronises s.
+// Times every configuration of the complex64 apply that serves the layout
+// (row pitch `pitch`: even -> the TMA kernel's, odd -> the cp.async
+// kernel's) on level lv with buffers x, y (nrhs fields of that layout,
+// caller-owned) and records the fastest in ctx.  Configurations with at least
+// twice nrhs RHS per CTA are skipped (their extra RHS are empty).  ms_out is
+// indexed by configuration id (1e300 for those not timed).  Synchronises s.
 int tune_cfg32(hx_ctx* ctx, const Level& lv, const float* v_dev, int nrhs, const void* x, void* y,
-               int ncalls, cudaStream_t s, int* best_cfg, double* ms_out, int ms_cap) {
-  const long long N = (long long)lv.n[0] * lv.n[1] * lv.n[2];
+               long long pitch, int ncalls, cudaStream_t s, int* best_cfg, double* ms_out, int ms_cap) {
+  const long long rstride = pitch * lv.n[1] * lv.n[2];
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  const int n = st32_num_configs();
+  const int n = cfg32_count();
+  const bool tma = (pitch & 1) == 0;
   std::vector<double> ms(n, 1e300);
   OpDesc<float> d = make_desc<float>(ctx, lv, v_dev, 0.5);   // the shifted form times the full row
-  for (int c = 0; c < n && e == cudaSuccess; ++c) {
-    e = launch_stencil32(d, kApply, c, x, nullptr, y, nrhs, N, 0.0, s);   // warm-up
+  d.pitch = pitch;
+  int best = -1;
+  for (int c = tma ? kZmCfgBase : 0; c < (tma ? n : kZmCfgBase) && e == cudaSuccess; ++c) {
+    if (cfg_rhs(c) > 1 && cfg_rhs(c) >= 2 * nrhs) continue;
+    d.cfg32 = c;
+    e = launch_stencil<float>(d, kApply, x, nullptr, y, nrhs, rstride, 0.0, s);   // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(e0, s);
     for (int k = 0; k < ncalls && e == cudaSuccess; ++k)
-      e = launch_stencil32(d, kApply, c, x, nullptr, y, nrhs, N, 0.0, s);
+      e = launch_stencil<float>(d, kApply, x, nullptr, y, nrhs, rstride, 0.0, s);
     if (e == cudaSuccess) e = cudaEventRecord(e1, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
     float t = 0;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-    if (e == cudaSuccess) ms[c] = t / ncalls;
+    if (e == cudaSuccess) {
+      ms[c] = t / ncalls;
+      if (best < 0 || ms[c] < ms[best]) best = c;
+    }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
-  int best = 0;
-  for (int c = 1; c < n; ++c)
-    if (ms[c] < ms[best]) best = c;
+  if (best < 0) return fail(ctx, HX_ERR_STATE, "autotune: no configuration timed");
   ctx->tuned[tune_key(lv.n[0], lv.n[1], lv.n[2], nrhs)] = best;
   if (best_cfg) *best_cfg = best;
   for (int c = 0; c < n && c < ms_cap && ms_out; ++c) ms_out[c] = ms[c];
@@ -105,7 +115,7 @@ extern "C" int hx_autotune(hx_ctx* ctx, const hx_grid* grid, const float* v_dev,
   cudaError_t e = cudaMalloc(&x, fb);
   if (e == cudaSuccess) e = cudaMalloc(&y, fb);
   if (e == cudaSuccess) e = cudaMemsetAsync(x, 0, fb, s);
-  if (e == cudaSuccess) st = tune_cfg32(ctx, *lv, v_dev, nrhs, x, y, ncalls, s, best_cfg, ms_out, ms_cap);
+  if (e == cudaSuccess) st = tune_cfg32(ctx, *lv, v_dev, nrhs, x, y, grid->nx, ncalls, s, best_cfg, ms_out, ms_cap);
   if (x) cudaFree(x);
   if (y) cudaFree(y);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune buffers");

@@ -117,12 +117,13 @@ __global__ void bicg_s_k(typename CT<T>::type* __restrict__ sv, const typename C
 
 // full weighting: coarse node I <- fine nodes 2I + s, s in {-1,0,1}^3, weight
 // prod_d (1/2)^{|s_d|} / 8; fine nodes outside the grid are zero.
+// fp: x-row pitch of the fine field (elements, >= fx).
 template <typename T>
-__global__ void restrict_k(const typename CT<T>::type* __restrict__ f, int fx, int fy, int fz,
+__global__ void restrict_k(const typename CT<T>::type* __restrict__ f, int fx, int fy, int fz, long long fp,
                            typename CT<T>::type* __restrict__ c, int cx, int cy, int cz) {
   pdl_enter();
   using C = typename CT<T>::type;
-  const long long Nc = (long long)cx * cy * cz, Nf = (long long)fx * fy * fz;
+  const long long Nc = (long long)cx * cy * cz, Nf = fp * fy * fz;
   const int r = blockIdx.y;
   for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < Nc;
        I += (long long)gridDim.x * blockDim.x) {
@@ -138,7 +139,7 @@ __global__ void restrict_k(const typename CT<T>::type* __restrict__ f, int fx, i
           const int x = 2 * X + sx;
           if (x < 0 || x >= fx) continue;
           const T w = (T)1 / (T)(8 << (abs(sx) + abs(sy) + abs(sz)));
-          acc = cfmar(w, f[(long long)r * Nf + ((long long)z * fy + y) * fx + x], acc);
+          acc = cfmar(w, f[(long long)r * Nf + ((long long)z * fy + y) * fp + x], acc);
         }
       }
     }
@@ -147,16 +148,18 @@ __global__ void restrict_k(const typename CT<T>::type* __restrict__ f, int fx, i
 }
 
 // trilinear prolongation added to the fine field
+// fp: x-row pitch of the fine field (elements, >= fx); padding is not written.
 template <typename T>
-__global__ void prolong_k(typename CT<T>::type* __restrict__ f, int fx, int fy, int fz,
+__global__ void prolong_k(typename CT<T>::type* __restrict__ f, int fx, int fy, int fz, long long fp,
                           const typename CT<T>::type* __restrict__ c, int cx, int cy, int cz) {
   pdl_enter();
   using C = typename CT<T>::type;
-  const long long Nc = (long long)cx * cy * cz, Nf = (long long)fx * fy * fz;
+  const long long Nc = (long long)cx * cy * cz, Nf = (long long)fx * fy * fz, Nfp = fp * fy * fz;
   const int r = blockIdx.y;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Nf;
        i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % fx), y = (int)((i / fx) % fy), z = (int)(i / ((long long)fx * fy));
+    const long long fi = ((long long)z * fy + y) * fp + x;
     int ix[2], iy[2], iz[2];
     T wx[2], wy[2], wz[2];
     auto split = [](int p, int nc, int* id, T* w) {
@@ -178,7 +181,7 @@ __global__ void prolong_k(typename CT<T>::type* __restrict__ f, int fx, int fy, 
           if (w != (T)0)
             acc = cfmar(w, c[(long long)r * Nc + ((long long)iz[a] * cy + iy[b]) * cx + ix[d]], acc);
         }
-    f[(long long)r * Nf + i] = cadd(f[(long long)r * Nf + i], acc);
+    f[(long long)r * Nfp + fi] = cadd(f[(long long)r * Nfp + fi], acc);
   }
 }
 
@@ -193,29 +196,33 @@ __global__ void inject_v_k(const float* __restrict__ vf, int fx, int fy, float* 
   }
 }
 
+// The complex64 side may use a padded x-row pitch p32 (rows of nx points);
+// the complex128 side is unpadded.  Padding is neither read nor written.
 __global__ void cast_scale_k(const double2* __restrict__ r64, float2* __restrict__ r32,
-                             const double* scale, long long N) {
+                             const double* scale, long long N, int nx, long long p32) {
   pdl_enter();
   const int k = blockIdx.y;
   const double s = scale[k];
-  const long long o = (long long)k * N;
+  const long long o = (long long)k * N, o32 = (long long)k * (N / nx) * p32;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
     const double2 a = r64[o + i];
-    r32[o + i] = make_float2((float)(a.x * s), (float)(a.y * s));
+    const long long row = i / nx;
+    r32[o32 + row * p32 + (i - row * nx)] = make_float2((float)(a.x * s), (float)(a.y * s));
   }
 }
 
 template <class D>
 __global__ void axpy_mixed_k(double2* __restrict__ x, const D* __restrict__ d,
-                             const double* scale, long long N) {
+                             const double* scale, long long N, int nx, long long pd) {
   pdl_enter();
   const int k = blockIdx.y;
   const double s = scale[k];
-  const long long o = (long long)k * N;
+  const long long o = (long long)k * N, od = (long long)k * (N / nx) * pd;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
        i += (long long)gridDim.x * blockDim.x) {
-    const D a = d[o + i];
+    const long long row = i / nx;
+    const D a = d[od + row * pd + (i - row * nx)];
     double2 v = x[o + i];
     v.x = fma(s, (double)a.x, v.x);
     v.y = fma(s, (double)a.y, v.y);
@@ -434,22 +441,22 @@ cudaError_t launch_bicg_s(void* sv, const void* r, const void* v, const double2*
 
 template <typename T>
 cudaError_t launch_restrict(const void* fine, const int nf[3], void* coarse, const int nc[3], int R,
-                            cudaStream_t s) {
+                            cudaStream_t s, long long fpitch) {
   using C = typename CT<T>::type;
   const long long Nc = (long long)nc[0] * nc[1] * nc[2];
-  (void)launch_k(restrict_k<T>, grid_for(Nc, R, 1), kThreads, 0, s, (const C*)fine, nf[0], nf[1], nf[2], (C*)coarse,
-                                                        nc[0], nc[1], nc[2]);
+  (void)launch_k(restrict_k<T>, grid_for(Nc, R, 1), kThreads, 0, s, (const C*)fine, nf[0], nf[1], nf[2],
+                 fpitch > 0 ? fpitch : (long long)nf[0], (C*)coarse, nc[0], nc[1], nc[2]);
   count_launch(1);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_prolong_add(void* fine, const int nf[3], const void* coarse, const int nc[3], int R,
-                               cudaStream_t s) {
+                               cudaStream_t s, long long fpitch) {
   using C = typename CT<T>::type;
   const long long Nf = (long long)nf[0] * nf[1] * nf[2];
-  (void)launch_k(prolong_k<T>, grid_for(Nf, R, 1), kThreads, 0, s, (C*)fine, nf[0], nf[1], nf[2], (const C*)coarse,
-                                                       nc[0], nc[1], nc[2]);
+  (void)launch_k(prolong_k<T>, grid_for(Nf, R, 1), kThreads, 0, s, (C*)fine, nf[0], nf[1], nf[2],
+                 fpitch > 0 ? fpitch : (long long)nf[0], (const C*)coarse, nc[0], nc[1], nc[2]);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -463,22 +470,23 @@ cudaError_t launch_inject_velocity(const float* vf, const int nf[3], float* vc, 
 }
 
 cudaError_t launch_cast_scale(const double2* r64, float2* r32, const double* scale, long long N, int R,
-                              cudaStream_t s) {
-  (void)launch_k(cast_scale_k, grid_for(N, R), kThreads, 0, s, r64, r32, scale, N);
+                              cudaStream_t s, int nx, long long p32) {
+  (void)launch_k(cast_scale_k, grid_for(N, R), kThreads, 0, s, r64, r32, scale, N, nx, p32 > 0 ? p32 : (long long)nx);
   count_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_mixed(double2* x64, const float2* d32, const double* scale, long long N, int R,
-                              cudaStream_t s) {
-  (void)launch_k(axpy_mixed_k<float2>, grid_for(N, R), kThreads, 0, s, x64, d32, scale, N);
+                              cudaStream_t s, int nx, long long p32) {
+  (void)launch_k(axpy_mixed_k<float2>, grid_for(N, R), kThreads, 0, s, x64, d32, scale, N, nx,
+                 p32 > 0 ? p32 : (long long)nx);
   count_launch(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_axpy_c128(double2* x64, const double2* d64, const double* scale, long long N, int R,
                              cudaStream_t s) {
-  (void)launch_k(axpy_mixed_k<double2>, grid_for(N, R), kThreads, 0, s, x64, d64, scale, N);
+  (void)launch_k(axpy_mixed_k<double2>, grid_for(N, R), kThreads, 0, s, x64, d64, scale, N, 1, 1LL);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -538,9 +546,9 @@ cudaError_t launch_bicg_xr_reduce(void* x, void* r, const void* sv, const void* 
   template cudaError_t launch_bicg_s<T>(void*, const void*, const void*, const double2*,           \
                                         long long, int, cudaStream_t);                             \
   template cudaError_t launch_restrict<T>(const void*, const int*, void*, const int*, int,         \
-                                          cudaStream_t);                                           \
+                                          cudaStream_t, long long);                                \
   template cudaError_t launch_prolong_add<T>(void*, const int*, const void*, const int*, int,      \
-                                             cudaStream_t);                                        \
+                                             cudaStream_t, long long);                                        \
   template cudaError_t launch_copy<T>(void*, const void*, long long, cudaStream_t);                \
   template cudaError_t launch_add_sources<T>(void*, long long, const SourceEntry*, int,            \
                                              cudaStream_t);

@@ -26,21 +26,24 @@ template <typename T>
 cudaError_t launch_bicg_s(void* sv, const void* r, const void* v, const double2* alpha, long long N,
                           int R, cudaStream_t s);
 // Multigrid transfers between a fine level (nf) and its coarse level (nc):
-// coarse = full weighting of fine;  fine += trilinear(coarse).
+// coarse = full weighting of fine;  fine += trilinear(coarse).  fpitch: x-row
+// pitch of the fine field (0: nf[0]); the coarse field is unpadded.
 template <typename T>
 cudaError_t launch_restrict(const void* fine, const int nf[3], void* coarse, const int nc[3], int R,
-                            cudaStream_t s);
+                            cudaStream_t s, long long fpitch = 0);
 template <typename T>
 cudaError_t launch_prolong_add(void* fine, const int nf[3], const void* coarse, const int nc[3],
-                               int R, cudaStream_t s);
+                               int R, cudaStream_t s, long long fpitch = 0);
 cudaError_t launch_inject_velocity(const float* vf, const int nf[3], float* vc, const int nc[3],
                                    cudaStream_t s);
 
 // r32[r,i] = (complex64)(r64[r,i] * scale[r]);  x64[r,i] += scale[r] * d32[r,i]
+// (N points per field in rows of nx; the complex64 fields use x-row pitch p32,
+// 0 = nx, and their padding is not touched)
 cudaError_t launch_cast_scale(const double2* r64, float2* r32, const double* scale, long long N,
-                              int R, cudaStream_t s);
+                              int R, cudaStream_t s, int nx, long long p32 = 0);
 cudaError_t launch_axpy_mixed(double2* x64, const float2* d32, const double* scale, long long N,
-                              int R, cudaStream_t s);
+                              int R, cudaStream_t s, int nx, long long p32 = 0);
 // x64[r,i] += scale[r] * d64[r,i]
 cudaError_t launch_axpy_c128(double2* x64, const double2* d64, const double* scale, long long N,
                              int R, cudaStream_t s);

@@ -245,7 +245,9 @@ def test_apply_batched_equals_single_applies(ctx, otable, cfg):
         bound = (abs(A) @ np.abs(xr).T).T
         assert np.all(np.isfinite(yy))
         assert np.max(np.abs(yy - ref) / bound) <= TOL[32]
-        if cfg >= 0:
+        if cfg >= 0 and g.nx % 2 == 1:
+            # odd nx: hx_apply_operator runs the same cp.async kernel (even nx takes
+            # the TMA kernel, which rounds in another order; checked against the oracle above)
             assert torch.equal(y, y1)
 
 
