@@ -404,10 +404,13 @@ def run_gpu(args):
         tr = _traffic_per_launch(dom)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr,
-                "kernel": {"apply32": "st32_kernel<kApply> (complex64)",
-                           "smooth32": "st32_kernel<kJacobi|kResidual> (complex64)",
+                "kernel": {"apply32": "complex64 z-marching stencil, y = A x (fine level)",
+                           "smooth32": "complex64 z-marching stencil, damped-Jacobi / residual sweeps of "
+                                       "the shifted operator (fine level)",
                            "apply64": "stencil_kernel<double, ...>",
                            "smooth64": "stencil_kernel<double, kJacobi|kResidual>"}[dom],
+                "kernel_choice": "the solver's autotuner picks the z-marching kernel and its launch "
+                                 "configuration per grid size and RHS count",
                 "launches": n, "algo_bytes_per_launch": by / n,
                 "share_of_step": round(ms / sum(prof_step_ms), 4),
                 "timed_in": "a second pass over the same steps with per-launch CUDA events",

@@ -328,15 +328,19 @@ int hx_assemble_csr_noalloc(hx_ctx* ctx, const hx_grid* grid, const float* v_dev
  * hx_stencil_sweep, hx_stencil_pitched and every complex64 stencil sweep of
  * hx_solve on grids above the direct-kernel size) runs on one of two
  * z-marching kernels, each in several launch configurations:
- *   ids 0-2: fields whose rows are not 16-byte aligned (odd nx, pitch = nx);
- *            per-thread asynchronous copies; 1, 2, 4 RHS per CTA;
- *   ids 3-8: rows of even pitch (the layout hx_solve uses); one
- *            tensor-memory-access copy per plane tile, the x/y-PML rows in a
- *            separate kernel; (8 rows, 1 / 2 / 4 / 8 RHS) and (16 rows,
- *            2 / 4 RHS) per CTA.
- * All compute the same operator (results differ only in FP32 rounding
- * order); their speed depends on the grid and nrhs.  A configuration that
- * does not serve a launch's layout is replaced by the automatic choice.  The
+ *   ids 0-2: any row pitch (the only kernel for odd pitches, e.g. odd nx);
+ *            per-thread asynchronous copies, x/y-PML rows in the same tiles;
+ *            1, 2, 4 RHS per CTA;
+ *   ids 3-8: even row pitch (16-byte rows: even nx, or the padded layout
+ *            hx_solve uses); one tensor-memory-access copy per plane tile,
+ *            the x/y-PML rows in a separate kernel; (8 rows, 1 / 2 / 4 / 8
+ *            RHS) and (16 rows, 2 / 4 RHS) per CTA.
+ * The automatic choice for an even pitch is the second kernel.  All compute
+ * the same operator (results differ only in FP32 rounding order); their
+ * speed depends on the grid and nrhs (the first is faster on small grids with
+ * thick PML, where the second kernel's separate PML rows weigh more).  A
+ * configuration that does not serve a launch's layout is replaced by the
+ * automatic choice.  The
  * paper has no counterpart (its solver is a sparse direct factorisation);
  * this only chooses between launch shapes.  hx_kernel_config_info returns
  * the number of configurations and, for a valid cfg, writes its rows per
@@ -350,7 +354,7 @@ int hx_kernel_config_info(int cfg, int* rows_per_thread, int* rhs_per_cta);
 int hx_set_kernel_config(hx_ctx* ctx, int cfg);
 
 /* Time every configuration of the complex64 apply that serves this grid's
- * own layout (pitch = nx: ids 3-8 for even nx, 0-2 for odd nx; shifted form,
+ * own layout (pitch = nx: all ids for even nx, 0-2 for odd nx; shifted form,
  * nrhs fields, one warm-up then ncalls launches each, CUDA events on stream;
  * configurations with at least twice nrhs RHS per CTA are skipped) on this
  * grid and velocity, and record the fastest for (nx, ny, nz, nrhs) in ctx;
@@ -403,7 +407,7 @@ typedef struct {
                             and replayed (not while hx_profile timing is on);
                             0: direct launches                                    */
   int autotune;          /* 1 (default): the first mixed solve of a grid size and
-                            nrhs with at least 2^20 point*RHS times the complex64
+                            nrhs with at least 2^18 point*RHS times the complex64
                             kernel configurations on the fine level (using the
                             solver's own buffers, before the solve) and keeps the
                             fastest in the context (see hx_autotune); 0: no     */

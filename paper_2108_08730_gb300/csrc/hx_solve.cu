@@ -697,7 +697,9 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   int lv_n[kMaxLev][3];
   const int nlev = plan_levels(n0, opt.mg_levels, lv_n);
   char key[256];
-  std::snprintf(key, sizeof(key), "%d %d %d r%d p%d L%d", grid->nx, grid->ny, grid->nz, nrhs, prec, nlev);
+  const bool variant = ctx->op_weights != HX_WEIGHTS_GA || ctx->op_mass_form != 2 || ctx->med_buoy || ctx->med_invq;
+  std::snprintf(key, sizeof(key), "%d %d %d r%d p%d L%d v%d", grid->nx, grid->ny, grid->nz, nrhs, prec, nlev,
+                variant ? 1 : 0);
   SolverImpl* S = nullptr;
   {
     auto it = ctx->solvers.find(key);
@@ -720,7 +722,9 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
         S->N[l] = (long long)lv_n[l][0] * lv_n[l][1] * lv_n[l][2];
       }
       const size_t cs = prec == 64 ? 16 : 8;
-      S->pitch0 = prec == 64 ? grid->nx : (grid->nx + 3) / 4 * 4;
+      // operator variants and media run on the one-thread-per-row kernel,
+      // which takes unpadded fields
+      S->pitch0 = prec == 64 || variant ? grid->nx : (grid->nx + 3) / 4 * 4;
       S->NP = S->pitch0 * grid->ny * grid->nz;
       const size_t fb = (size_t)nrhs * S->NP * cs;
       cudaError_t e = cudaSuccess;
@@ -873,7 +877,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "setup"));
   // complex64 kernel configuration of the fine level, tuned once per grid
   // size and nrhs (the Krylov buffers serve as scratch before the solve)
-  if (prec == 32 && opt.autotune && (long long)N * nrhs >= (1LL << 20) &&
+  if (prec == 32 && opt.autotune && (long long)N * nrhs >= (1LL << 18) &&
       ctx->st32_cfg < 0 && !ctx->tuned.count(tune_key(grid->nx, grid->ny, grid->nz, nrhs))) {
     if ((e = cudaMemsetAsync(S->p.p, 0, (size_t)nrhs * S->NP * 8, stream)))
       return finish(cuda_fail(ctx, e, "autotune scratch"));

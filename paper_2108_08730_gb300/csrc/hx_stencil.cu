@@ -533,22 +533,32 @@ cudaError_t launch_stencil(const OpDesc<T>& op, int mode, const void* x, const v
     if (rstride != (long long)op.nx * op.ny * op.nz) return cudaErrorInvalidValue;
     return launch_direct_stencil<T>(op, mode, x, b, y, nrhs, omega_j, s);
   }
-  // complex64 fields with 16-byte rows: the TMA z-marching kernel
-  if (sizeof(T) == 4 && (field_pitch(op) & 1) == 0 && ((uintptr_t)x & 15) == 0 && ((uintptr_t)b & 15) == 0) {
+  if (sizeof(T) == 4) {
+    // complex64: the two z-marching kernels.  Configuration ids 0-2 select
+    // the cp.async kernel (any row pitch), ids 3.. the tensor-copy kernel
+    // (even pitch, 16-byte aligned x and b); -1 lets an even pitch take the
+    // tensor-copy kernel.  The first Jacobi sweep of padded fields is the
+    // pitched per-row kernel of hx_zmarch.cu.
     const OpDesc<float>& of = reinterpret_cast<const OpDesc<float>&>(op);
     const long long pitch = field_pitch(op);
     if (rstride != pitch * op.ny * op.nz) return cudaErrorInvalidValue;
     int dev = 0;
     cudaGetDevice(&dev);
-    const int zc = op.cfg32 >= kZmCfgBase ? op.cfg32 - kZmCfgBase : -1;
-    return launch_zmarch(of, mode, zc, x, b, y, nrhs, pitch, omega_j, zm_error_flag(dev), s);
-  }
-  if (op.pitch > 0 && op.pitch != op.nx) return cudaErrorInvalidValue;   // odd pitch: not supported
-  // the complex64 kernel's bulk row copies need a 16-byte aligned x
-  if (sizeof(T) == 4 && mode != kJacobi0 && ((uintptr_t)x & 15) == 0) {
-    const int cfg = op.cfg32 >= 0 && op.cfg32 < kZmCfgBase ? op.cfg32 : st32_default_config(nrhs);
-    return launch_stencil32(reinterpret_cast<const OpDesc<float>&>(op), mode, cfg, x, b, y, nrhs,
-                            rstride, omega_j, s);
+    const bool even = (pitch & 1) == 0;
+    if (mode == kJacobi0 && pitch != op.nx)
+      return even ? launch_zmarch(of, kJacobi0, -1, x, b, y, nrhs, pitch, omega_j, nullptr, s)
+                  : cudaErrorInvalidValue;
+    if (mode != kJacobi0) {
+      const bool want_cp = op.cfg32 >= 0 && op.cfg32 < kZmCfgBase;
+      if (even && !want_cp && ((uintptr_t)x & 15) == 0 && ((uintptr_t)b & 15) == 0)
+        return launch_zmarch(of, mode, op.cfg32 >= kZmCfgBase ? op.cfg32 - kZmCfgBase : -1, x, b, y, nrhs, pitch,
+                             omega_j, zm_error_flag(dev), s);
+      // the cp.async kernel's row copies need a 16-byte aligned x
+      if (((uintptr_t)x & 15) == 0)
+        return launch_stencil32(of, mode, want_cp ? op.cfg32 : st32_default_config(nrhs), x, b, y, nrhs, rstride,
+                                omega_j, s);
+    }
+    if (pitch != op.nx) return cudaErrorInvalidValue;
   }
   switch (mode) {
     case kApply: return launch_m<T, kApply>(op, x, b, y, nrhs, rstride, omega_j, s);

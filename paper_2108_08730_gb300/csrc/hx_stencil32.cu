@@ -157,7 +157,9 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
   }
   const int z0 = zc * zlen, z1 = min(nz, z0 + zlen);
   if (z0 >= nz) return;                                // a chunk index past a long-chunk tile's end
-  const long long plane = (long long)nx * ny;
+  // fields: x-row pitch op.pitch (0: nx); the velocity is unpadded
+  const long long fpitch = op.pitch > 0 ? op.pitch : nx;
+  const long long plane = fpitch * ny, vplane = (long long)nx * ny;
   const bool shift = op.beta != 0.f;
 
   // ---- loader.  This thread copies elements tid + k kThr of every plane
@@ -176,7 +178,7 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
       const int ly = e / kPW, lx = e - ly * kPW;
       const int gx = gx0 + lx - 1, gy = gy0 + ly - 1;
       ld_in[k] = e < K::PLANE && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-      ld_p[k] = ld_in[k] ? xr + (gy * nx + gx) : x;
+      ld_p[k] = ld_in[k] ? xr + (gy * fpitch + gx) : x;
     }
   }
   // copies of plane z (all RB fields) into the slot at byte offset so; planes
@@ -280,14 +282,15 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
     // the general form is exact for every row: a warp holding any x/y PML
     // row runs it on all lanes rather than running both forms
     plain_xy[j] = !__any_sync(0xffffffffu, act[j] && !(plain_x && iy >= op.plain_lo[1] && iy <= op.plain_hi[1]));
-    const long long o = (long long)z0 * plane + (long long)(act[j] ? iy * nx + ix : 0);
+    const long long ov = (long long)z0 * vplane + (long long)(act[j] ? iy * nx + ix : 0);
+    const long long o = (long long)z0 * plane + (long long)(act[j] ? iy * fpitch + ix : 0);
     if (K::PREFETCH) {
-      tab_fetch(act[j] && z0 < z1 ? __ldg(op.v + o) : 1.5e3f, tnext[j]);
-      v1[j] = act[j] && z0 + 1 < z1 ? __ldg(op.v + o + plane) : 1.5e3f;
-      vp[j] = op.v + o + 2 * plane;
+      tab_fetch(act[j] && z0 < z1 ? __ldg(op.v + ov) : 1.5e3f, tnext[j]);
+      v1[j] = act[j] && z0 + 1 < z1 ? __ldg(op.v + ov + vplane) : 1.5e3f;
+      vp[j] = op.v + ov + 2 * vplane;
     } else {
-      v1[j] = act[j] && z0 < z1 ? __ldg(op.v + o) : 1.5e3f;
-      vp[j] = op.v + o + plane;
+      v1[j] = act[j] && z0 < z1 ? __ldg(op.v + ov) : 1.5e3f;
+      vp[j] = op.v + ov + vplane;
     }
     yo[j] = o + (long long)r0 * rstride;
     bnx[j] = BPF && b && act[j] && z0 < z1 ? b[yo[j]] : make_float2(0.f, 0.f);
@@ -312,7 +315,7 @@ __device__ __forceinline__ void st32_tile(const OpDesc<float>& op, const float2*
         tab_fetch(v1[j], t);                           // v1 holds v at plane z here
       }
       v1[j] = act[j] && z + (K::PREFETCH ? 2 : 1) < z1 ? __ldg(vp[j]) : 1.5e3f;
-      vp[j] += plane;
+      vp[j] += vplane;
       const long long off = yo[j];
       yo[j] += plane;
       float2 bcur = make_float2(0.f, 0.f);

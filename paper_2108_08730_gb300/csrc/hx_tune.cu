@@ -49,11 +49,12 @@ extern "C" int hx_set_kernel_config(hx_ctx* ctx, int cfg) {
 namespace hx {
 
 // Times every configuration of the complex64 apply that serves the layout
-// (row pitch `pitch`: even -> the TMA kernel's, odd -> the cp.async
-// kernel's) on level lv with buffers x, y (nrhs fields of that layout,
-// caller-owned) and records the fastest in ctx.  Configurations with at least
-// twice nrhs RHS per CTA are skipped (their extra RHS are empty).  ms_out is
-// indexed by configuration id (1e300 for those not timed).  Synchronises s.
+// (row pitch `pitch`: even -> both kernels' configurations, odd -> the
+// cp.async kernel's) on level lv with buffers x, y (nrhs fields of that
+// layout, caller-owned) and records the fastest in ctx.  Configurations with
+// at least twice nrhs RHS per CTA are skipped (their extra RHS are empty).
+// ms_out is indexed by configuration id (1e300 for those not timed).
+// Synchronises s.
 int tune_cfg32(hx_ctx* ctx, const Level& lv, const float* v_dev, int nrhs, const void* x, void* y,
                long long pitch, int ncalls, cudaStream_t s, int* best_cfg, double* ms_out, int ms_cap) {
   const long long rstride = pitch * lv.n[1] * lv.n[2];
@@ -66,7 +67,7 @@ int tune_cfg32(hx_ctx* ctx, const Level& lv, const float* v_dev, int nrhs, const
   OpDesc<float> d = make_desc<float>(ctx, lv, v_dev, 0.5);   // the shifted form times the full row
   d.pitch = pitch;
   int best = -1;
-  for (int c = tma ? kZmCfgBase : 0; c < (tma ? n : kZmCfgBase) && e == cudaSuccess; ++c) {
+  for (int c = 0; c < (tma ? n : kZmCfgBase) && e == cudaSuccess; ++c) {
     if (cfg_rhs(c) > 1 && cfg_rhs(c) >= 2 * nrhs) continue;
     d.cfg32 = c;
     e = launch_stencil<float>(d, kApply, x, nullptr, y, nrhs, rstride, 0.0, s);   // warm-up
