@@ -359,7 +359,10 @@ int hx_set_kernel_config(hx_ctx* ctx, int cfg);
  * configurations with at least twice nrhs RHS per CTA are skipped) on this
  * grid and velocity, and record the fastest for (nx, ny, nz, nrhs) in ctx;
  * later hx_apply_operator / hx_solve launches of that size use it (hx_solve
- * tunes its own padded layout itself when this size has no entry).
+ * tunes its own padded layout itself when this size has no entry).  The
+ * damped-Jacobi sweep of the shifted operator is timed the same way and its
+ * fastest configuration recorded apart, for the sweeps (hx_stencil_sweep and
+ * the solver's smoother); best_cfg and ms_out report the apply.
  *   best_cfg: receives the chosen configuration (may be NULL);
  *   ms_out:   receives up to ms_cap per-launch times in ms, by configuration
  *             id (1e300 for configurations not timed; may be NULL).

@@ -448,7 +448,7 @@ int hx_stencil_sweep(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, doubl
   cudaError_t e;
   if (precision == 32) {
     OpDesc<float> d = make_desc<float>(ctx, *lv, v_dev, shift_beta);
-    d.cfg32 = ctx_cfg32(ctx, grid->nx, grid->ny, grid->nz, nrhs);
+    d.cfg32 = ctx_cfg32(ctx, grid->nx, grid->ny, grid->nz, nrhs, true);
     e = launch_stencil(d, mode, x_dev, b_dev, y_dev, nrhs, N, omega, s);
   } else {
     const OpDesc<double> d = make_desc<double>(ctx, *lv, v_dev, shift_beta);
@@ -481,7 +481,7 @@ int hx_stencil_pitched(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, dou
   if ((st = get_level(ctx, grid, nl, grid->h, &lv))) return st;
   const int mode = kind == 0 ? kApply : (kind == HX_SWEEP_RESIDUAL ? kResidual : kJacobi);
   OpDesc<float> d = make_desc<float>(ctx, *lv, v_dev, shift_beta);
-  d.cfg32 = ctx_cfg32(ctx, grid->nx, grid->ny, grid->nz, nrhs);
+  d.cfg32 = ctx_cfg32(ctx, grid->nx, grid->ny, grid->nz, nrhs, kind != 0);
   d.pitch = pitch;
   const cudaError_t e = launch_stencil(d, mode, x_dev, kind == 0 ? nullptr : b_dev, y_dev, nrhs,
                                        (long long)pitch * grid->ny * grid->nz, omega, (cudaStream_t)stream);

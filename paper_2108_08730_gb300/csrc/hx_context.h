@@ -98,8 +98,9 @@ int fail(hx_ctx* ctx, int code, const std::string& msg);
 inline std::string tune_key(int nx, int ny, int nz, int nrhs) {
   return std::to_string(nx) + "x" + std::to_string(ny) + "x" + std::to_string(nz) + "r" + std::to_string(nrhs);
 }
-// complex64 kernel configuration for a launch on ctx (forced, tuned, or -1)
-int ctx_cfg32(const hx_ctx* ctx, int nx, int ny, int nz, int nrhs);
+// complex64 kernel configuration for a launch on ctx (forced, tuned, or -1);
+// sweep: a residual / Jacobi sweep (tuned apart from y = A x)
+int ctx_cfg32(const hx_ctx* ctx, int nx, int ny, int nz, int nrhs, bool sweep = false);
 // autotuner core (hx_tune.cu): times the configurations on level lv with
 // caller-owned buffers and records the fastest for (level size, nrhs)
 int tune_cfg32(hx_ctx* ctx, const Level& lv, const float* v_dev, int nrhs, const void* x, void* y,

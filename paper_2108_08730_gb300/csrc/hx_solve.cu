@@ -197,7 +197,7 @@ class Run {
   template <typename T>
   OpDesc<T> desc(int l, double beta) const {
     OpDesc<T> d = make_desc<T>(ctx, *S->lvl[l], l == 0 ? v_fine : (const float*)S->vlev[l].p, beta, true);
-    d.cfg32 = ctx_cfg32(ctx, S->n[l][0], S->n[l][1], S->n[l][2], S->R);
+    d.cfg32 = ctx_cfg32(ctx, S->n[l][0], S->n[l][1], S->n[l][2], S->R, true);
     if (l == 0) d.pitch = S->pitch0;
     return d;
   }

@@ -14,9 +14,9 @@
 
 namespace hx {
 
-int ctx_cfg32(const hx_ctx* ctx, int nx, int ny, int nz, int nrhs) {
+int ctx_cfg32(const hx_ctx* ctx, int nx, int ny, int nz, int nrhs, bool sweep) {
   if (ctx->st32_cfg >= 0) return ctx->st32_cfg;
-  auto it = ctx->tuned.find(tune_key(nx, ny, nz, nrhs));
+  auto it = ctx->tuned.find(tune_key(nx, ny, nz, nrhs) + (sweep ? "s" : ""));
   return it == ctx->tuned.end() ? -1 : it->second;
 }
 
@@ -63,30 +63,38 @@ int tune_cfg32(hx_ctx* ctx, const Level& lv, const float* v_dev, int nrhs, const
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   const int n = cfg32_count();
   const bool tma = (pitch & 1) == 0;
-  std::vector<double> ms(n, 1e300);
-  OpDesc<float> d = make_desc<float>(ctx, lv, v_dev, 0.5);   // the shifted form times the full row
-  d.pitch = pitch;
-  int best = -1;
+  std::vector<double> ms(n, 1e300), ms_sweep(n, 1e300);
+  // y = A x (the Krylov operator), and the damped-Jacobi sweep of the shifted
+  // operator (the smoother; x serves as its b), timed and chosen apart
+  OpDesc<float> da = make_desc<float>(ctx, lv, v_dev, 0.0), dj = make_desc<float>(ctx, lv, v_dev, 0.5);
+  da.pitch = dj.pitch = pitch;
+  int best = -1, best_sweep = -1;
   for (int c = 0; c < (tma ? n : kZmCfgBase) && e == cudaSuccess; ++c) {
     if (cfg_rhs(c) > 1 && cfg_rhs(c) >= 2 * nrhs) continue;
-    d.cfg32 = c;
-    e = launch_stencil<float>(d, kApply, x, nullptr, y, nrhs, rstride, 0.0, s);   // warm-up
-    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
-    for (int k = 0; k < ncalls && e == cudaSuccess; ++k)
-      e = launch_stencil<float>(d, kApply, x, nullptr, y, nrhs, rstride, 0.0, s);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float t = 0;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-    if (e == cudaSuccess) {
-      ms[c] = t / ncalls;
-      if (best < 0 || ms[c] < ms[best]) best = c;
+    for (int sweep = 0; sweep < 2 && e == cudaSuccess; ++sweep) {
+      OpDesc<float>& d = sweep ? dj : da;
+      d.cfg32 = c;
+      const int mode = sweep ? kJacobi : kApply;
+      const void* b = sweep ? x : nullptr;
+      e = launch_stencil<float>(d, mode, x, b, y, nrhs, rstride, 0.6, s);   // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      for (int k = 0; k < ncalls && e == cudaSuccess; ++k) e = launch_stencil<float>(d, mode, x, b, y, nrhs, rstride, 0.6, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float t = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+      if (e != cudaSuccess) break;
+      std::vector<double>& m = sweep ? ms_sweep : ms;
+      int& bst = sweep ? best_sweep : best;
+      m[c] = t / ncalls;
+      if (bst < 0 || m[c] < m[bst]) bst = c;
     }
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune");
-  if (best < 0) return fail(ctx, HX_ERR_STATE, "autotune: no configuration timed");
+  if (best < 0 || best_sweep < 0) return fail(ctx, HX_ERR_STATE, "autotune: no configuration timed");
+  ctx->tuned[tune_key(lv.n[0], lv.n[1], lv.n[2], nrhs) + "s"] = best_sweep;
   ctx->tuned[tune_key(lv.n[0], lv.n[1], lv.n[2], nrhs)] = best;
   if (best_cfg) *best_cfg = best;
   for (int c = 0; c < n && c < ms_cap && ms_out; ++c) ms_out[c] = ms[c];
