@@ -390,7 +390,7 @@ typedef struct {
   double shift_beta;     /* complex shift of the preconditioner (default 1.0)    */
   int mg_levels;         /* multigrid levels incl. the fine grid; 0 = automatic   */
   int nu_pre, nu_post;   /* damped-Jacobi sweeps before / after coarse correction
-                            (default 2, 2)                                        */
+                            (default 3, 3)                                        */
   int coarse_sweeps;     /* damped-Jacobi sweeps on the coarsest level when it is
                             not solved exactly (default 4)                        */
   double omega_jacobi;   /* Jacobi damping (default 0.6)                          */
