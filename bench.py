@@ -71,7 +71,7 @@ def _args():
     p.add_argument("--kernel-workload", default="tectonic")
     p.add_argument("--kernel-nrhs", type=int, default=4)
     p.add_argument("--kernel-prec", type=int, default=32, choices=[32, 64])
-    p.add_argument("--serve-requests", type=int, default=12,
+    p.add_argument("--serve-requests", type=int, default=40,
                    help="Poisson-arriving requests of the serving workload (0: skip)")
     p.add_argument("--serve-slots", type=int, default=4)
     p.add_argument("--serve-deadline", type=float, default=30.0,
@@ -240,10 +240,10 @@ def _traffic_per_launch(kind):
         return None
     try:
         rec = json.load(open(path))
-        src = os.path.join(ROOT, "paper_2108_08730_gb300", "csrc", "hx_stencil32.cu")
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        if rec.get("source_sha") != h:
-            return None
+        for src, sha in rec.get("sources", {}).items():
+            h = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+            if h != sha:
+                return None
         return rec.get(kind, {}).get("bytes_per_launch_full_size")
     except Exception:
         return None
