@@ -422,6 +422,10 @@ typedef struct {
                             synchronises anyway; once non-zero the solve stops
                             with HX_ERR_CANCELLED and the best iterate.  Another
                             thread may set it at any time.  NULL (default)     */
+  int nu_coarse;         /* > 0: damped-Jacobi sweeps before and after the coarse
+                            correction on the levels below the fine one (the
+                            fine level keeps nu_pre / nu_post); 0 (default):
+                            nu_pre / nu_post on every level                     */
 } hx_solve_opts;
 
 typedef struct {

@@ -239,8 +239,10 @@ class Run {
       HX_CK(launch_dense_matvec<T>(S->cinv.p, b, e, N, R, stream));
       return HX_OK;
     }
-    const int pre = coarsest ? opt.coarse_sweeps : opt.nu_pre;
-    const int swaps = (pre - 1) + (coarsest ? 0 : opt.nu_post);
+    const int nu1 = l > 0 && opt.nu_coarse > 0 ? opt.nu_coarse : opt.nu_pre;
+    const int nu2 = l > 0 && opt.nu_coarse > 0 ? opt.nu_coarse : opt.nu_post;
+    const int pre = coarsest ? opt.coarse_sweeps : nu1;
+    const int swaps = (pre - 1) + (coarsest ? 0 : nu2);
     void* cur = swaps % 2 == 0 ? e : w;
     void* oth = swaps % 2 == 0 ? w : e;
     HX_CK(stencil<T>(l, op, kJacobi0, nullptr, b, cur, opt.omega_jacobi));
@@ -254,7 +256,7 @@ class Run {
       int st = vcycle<T>(l + 1, S->mb[l + 1].p, S->me[l + 1].p, S->mw[l + 1].p);
       if (st) return st;
       HX_CK(launch_prolong_add<T>(cur, S->n[l], S->me[l + 1].p, S->n[l + 1], R, stream, l == 0 ? S->pitch0 : 0));
-      for (int k = 0; k < opt.nu_post; ++k) {
+      for (int k = 0; k < nu2; ++k) {
         HX_CK(stencil<T>(l, op, kJacobi, cur, b, oth, opt.omega_jacobi));
         std::swap(cur, oth);
       }
@@ -470,6 +472,7 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->autotune = 1;
   o->time_limit_s = 0.0;
   o->cancel = nullptr;
+  o->nu_coarse = 0;
 }
 
 namespace {
@@ -652,7 +655,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       !(opt.omega_jacobi > 0 && opt.omega_jacobi < 2) || !(opt.shift_beta >= 0) ||
       opt.check_every < 1 || opt.coarse_galerkin < 0 || opt.coarse_galerkin > 1 ||
       !(opt.pml_cap >= 0) || opt.use_graphs < 0 || opt.use_graphs > 1 ||
-      opt.autotune < 0 || opt.autotune > 1 || !(opt.time_limit_s >= 0) || opt.mg_levels < 0 ||
+      opt.autotune < 0 || opt.autotune > 1 || !(opt.time_limit_s >= 0) || opt.mg_levels < 0 || opt.nu_coarse < 0 ||
       opt.mg_levels > kMaxLev)
     return finish(fail(ctx, HX_ERR_ARG, "invalid solve options"));
   std::vector<int> has_src(nrhs, 0);
