@@ -71,11 +71,13 @@ def _args():
     p.add_argument("--kernel-workload", default="tectonic")
     p.add_argument("--kernel-nrhs", type=int, default=4)
     p.add_argument("--kernel-prec", type=int, default=32, choices=[32, 64])
-    p.add_argument("--serve-requests", type=int, default=40,
+    p.add_argument("--serve-requests", type=int, default=110,
                    help="Poisson-arriving requests of the serving workload (0: skip)")
     p.add_argument("--serve-slots", type=int, default=4)
     p.add_argument("--serve-deadline", type=float, default=30.0,
-                   help="per-request solve time limit in s (hx_solve_opts.time_limit_s)")
+                   help="base of the per-request solve time limit in s (hx_solve_opts.time_limit_s): "
+                        "each request gets this plus its own time at 1/slots of the measured solo "
+                        "capacity")
     p.add_argument("--serve-only", action="store_true", help="run the serving workload alone")
     p.add_argument("--solve-config", default=None, choices=["homogeneous", "linear_gradient",
                                                              "sharp_contrast", "tectonic"],
@@ -585,17 +587,17 @@ def run_serving(args, T, nreq=None, seed0=5000, log=None):
     work = np.array([r.n_points * r.nrhs for r in reqs], dtype=np.float64)
     srv = B.Server(T, slots=args.serve_slots)
 
-    def submit(k, wl):
+    def submit(k, wl, limit):
         out = np.zeros((wl.nrhs,) + wl.shape, dtype=np.complex128)
         t = srv.submit(B.grid_of(wl), wl.v, B.sources_of(wl), wl.nrhs, out, model_id=seed0 + k,
-                       time_limit_s=args.serve_deadline)
+                       time_limit_s=limit)
         return t, out
 
     # solo capacity: the first requests one at a time (also warms the engine)
     ncal = min(3, nreq)
     t0 = time.perf_counter()
     for k in range(ncal):
-        t, _ = submit(k, reqs[k])
+        t, _ = submit(k, reqs[k], 4 * args.serve_deadline)
         r = srv.wait(t)
         if r["status"] != 0:
             raise RuntimeError(f"serving calibration request {k} failed: {r}")
@@ -606,18 +608,23 @@ def run_serving(args, T, nreq=None, seed0=5000, log=None):
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
     tickets = []
     start = time.perf_counter()
+    # a runaway guard scaled to the request: the base plus the time the request
+    # takes with the GPU shared among the slots
+    limits = [args.serve_deadline + args.serve_slots * w / solo for w in work]
     for k, wl in enumerate(reqs):
         dt = arrivals[k] - (time.perf_counter() - start)
         if dt > 0:
             time.sleep(dt)
-        tickets.append(submit(k, wl))
+        tickets.append(submit(k, wl, limits[k]))
     res = [srv.wait(t) for t, _ in tickets]
     st = srv.stats()
     srv.close()
     bad = [seed0 + k for k, r in enumerate(res) if r["status"] != 0]
     iters = [r["report"]["inner_iters"] for r in res]
     return {"requests": nreq, "slots": args.serve_slots, "completed": st["completed"],
-            "failed": len(bad), "failed_seeds": bad, "deadline_s": args.serve_deadline,
+            "failed": len(bad), "failed_seeds": bad,
+            "deadline_s": f"{args.serve_deadline:g} + {args.serve_slots} x point*RHS / solo capacity "
+                          f"({min(limits):.1f} .. {max(limits):.1f} s)",
             "inner_iters_median": float(np.median(iters)), "inner_iters_max": int(max(iters)),
             "arrival_rate_per_s": round(rate, 4), "offered_load": 0.8,
             "solo_capacity_mpoint_rhs_s": round(solo / 1e6, 3),

@@ -400,11 +400,16 @@ typedef struct {
   int coarse_galerkin;   /* 1: coarse operators R A P (Galerkin); 0 (default):
                             the stencil rediscretised at 2^l h                    */
   double pml_cap;        /* the preconditioner's PML damping is capped at
-                            gamma <= pml_cap * omega (default 1; 0 = no cap).
-                            Damped Jacobi diverges where the stretching rotates
-                            one axis's coefficients far from the others; the
-                            preconditioner only has to approximate A^-1, and the
-                            Krylov operator keeps the true PML.                   */
+                            gamma <= cap * omega.  pml_cap > 0: cap = pml_cap;
+                            0: no cap; < 0 (default -15): cap =
+                            min(1, |pml_cap| omega / gamma0), gamma0 the
+                            largest damping of the grid's PML faces (tighter
+                            for thin, strongly damped layers at low
+                            frequency).  Damped Jacobi diverges where the
+                            stretching rotates one axis's coefficients far from
+                            the others; the preconditioner only has to
+                            approximate A^-1, and the Krylov operator keeps the
+                            true PML.                                           */
   int use_graphs;        /* 1 (default): each block of check_every Krylov
                             iterations is captured once per call as a CUDA graph
                             and replayed (not while hx_profile timing is on);
@@ -422,9 +427,9 @@ typedef struct {
                             synchronises anyway; once non-zero the solve stops
                             with HX_ERR_CANCELLED and the best iterate.  Another
                             thread may set it at any time.  NULL (default)     */
-  int nu_coarse;         /* > 0: damped-Jacobi sweeps before and after the coarse
-                            correction on the levels below the fine one (the
-                            fine level keeps nu_pre / nu_post); 0 (default):
+  int nu_coarse;         /* > 0 (default 2): damped-Jacobi sweeps before and after
+                            the coarse correction on the levels below the fine
+                            one (the fine level keeps nu_pre / nu_post); 0:
                             nu_pre / nu_post on every level                     */
 } hx_solve_opts;
 

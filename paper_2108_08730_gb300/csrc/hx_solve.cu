@@ -467,12 +467,12 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->initial_guess = 0;
   o->check_every = 2;
   o->coarse_galerkin = 0;
-  o->pml_cap = 1.0;
+  o->pml_cap = -15.0;   // automatic: min(1, 15 omega / gamma0), see hx_solve_opts
   o->use_graphs = 1;
   o->autotune = 1;
   o->time_limit_s = 0.0;
   o->cancel = nullptr;
-  o->nu_coarse = 0;
+  o->nu_coarse = 2;
 }
 
 namespace {
@@ -654,7 +654,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       opt.max_outer < 1 || opt.nu_pre < 1 || opt.nu_post < 0 || opt.coarse_sweeps < 1 ||
       !(opt.omega_jacobi > 0 && opt.omega_jacobi < 2) || !(opt.shift_beta >= 0) ||
       opt.check_every < 1 || opt.coarse_galerkin < 0 || opt.coarse_galerkin > 1 ||
-      !(opt.pml_cap >= 0) || opt.use_graphs < 0 || opt.use_graphs > 1 ||
+      !std::isfinite(opt.pml_cap) || opt.use_graphs < 0 || opt.use_graphs > 1 ||
       opt.autotune < 0 || opt.autotune > 1 || !(opt.time_limit_s >= 0) || opt.mg_levels < 0 || opt.nu_coarse < 0 ||
       opt.mg_levels > kMaxLev)
     return finish(fail(ctx, HX_ERR_ARG, "invalid solve options"));
@@ -779,11 +779,24 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       ctx->solver_lru.push_front(key);
     }
   }
+  // ---- the preconditioner's PML cap: fixed, or (pml_cap < 0) tighter the more
+  // strongly the grid's PML damps: min(1, |pml_cap| omega / gamma0), gamma0
+  // the largest damping of the grid's PML faces
+  double pml_cap = opt.pml_cap;
+  if (pml_cap < 0) {
+    const double omega = 2.0 * M_PI * grid->f;
+    double ratio = 0;
+    for (int k = 0; k < 6; ++k)
+      if (grid->npml[k] > 0)
+        ratio = std::max(ratio, 3.0 * grid->v_ref / (2.0 * grid->npml[k] * grid->h) * std::log(1.0 / grid->r_coef) /
+                                    omega);
+    pml_cap = ratio > 0 ? std::min(1.0, -opt.pml_cap / ratio) : 1.0;
+  }
   // ---- operator levels (PML arrays depend on h, f, npml, v_ref, r_coef)
   char okey[320];
   std::snprintf(okey, sizeof(okey), "%.17g %.17g %d %d %d %d %d %d %.17g %.17g cap%.17g", grid->h, grid->f,
                 grid->npml[0], grid->npml[1], grid->npml[2], grid->npml[3], grid->npml[4], grid->npml[5],
-                grid->v_ref, grid->r_coef, opt.pml_cap);
+                grid->v_ref, grid->r_coef, pml_cap);
   if (S->op_key != okey) {
     // private copies, so LRU eviction in the shared cache cannot free them:
     // lvlA = the true fine operator (Krylov apply, FP64 residual); lvl[l] =
@@ -811,7 +824,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
     };
     if ((st = own_copy(S->n[0], grid->h, 0.0, &S->lvlA))) return finish(st);
     for (int l = 0; l < S->nlev; ++l)
-      if ((st = own_copy(S->n[l], grid->h * (double)(1 << l), opt.pml_cap, &S->lvl[l]))) return finish(st);
+      if ((st = own_copy(S->n[l], grid->h * (double)(1 << l), pml_cap, &S->lvl[l]))) return finish(st);
     S->op_key = okey;
   }
   // coarse velocities by injection
