@@ -88,6 +88,10 @@ def _args():
                         "shifted operator (beta = 1, omega = 0.6), as inside the solve")
     p.add_argument("--kernel-cfg", default="auto",
                    help="complex64 kernel configuration: auto, tune, all, or an id")
+    p.add_argument("--kernel-layout", default="plain", choices=["plain", "padded"],
+                   help="plain: (nrhs, nz, ny, nx) fields through hx_apply_operator / "
+                        "hx_stencil_sweep;  padded: complex64 rows padded to a multiple of 4 "
+                        "(the solver's layout) through hx_stencil_pitched")
     p.add_argument("--large", default="tectonic,sharp_contrast",
                    help="comma-separated large batched workloads solved once each with all their "
                         "sources (RHS split over the ranks) plus the stencil roofline at that size; "
@@ -620,9 +624,14 @@ def run_serving(args, T, nreq=None, seed0=5000, log=None):
     st = srv.stats()
     srv.close()
     bad = [seed0 + k for k, r in enumerate(res) if r["status"] != 0]
+    failures = [{"seed": seed0 + k, "status": r["status"], "inner_iters": r["report"]["inner_iters"],
+                 "outer_iters": r["report"]["outer_iters"], "rel_residual": r["report"]["rel_residual"],
+                 "queue_ms": round(r["queue_ms"], 1), "run_ms": round(r["run_ms"], 1),
+                 "limit_s": round(limits[k], 1)}
+                for k, r in enumerate(res) if r["status"] != 0]
     iters = [r["report"]["inner_iters"] for r in res]
     return {"requests": nreq, "slots": args.serve_slots, "completed": st["completed"],
-            "failed": len(bad), "failed_seeds": bad,
+            "failed": len(bad), "failed_seeds": bad, "failures": failures,
             "deadline_s": f"{args.serve_deadline:g} + {args.serve_slots} x point*RHS / solo capacity "
                           f"({min(limits):.1f} .. {max(limits):.1f} s)",
             "inner_iters_median": float(np.median(iters)), "inner_iters_max": int(max(iters)),
@@ -678,9 +687,11 @@ def run_solve_config(args):
 
 
 def run_kernel(args):
-    """Time hx_apply_operator alone (complex64 or complex128) on a full-size
+    """Time one operator kernel alone (complex64 or complex128) on a full-size
     model: --kernel-workload (tectonic 401x401x187 by default) with
-    --kernel-nrhs right-hand sides; L2 flushed before every timed launch."""
+    --kernel-nrhs right-hand sides, --kernel-mode apply or a sweep, plain
+    fields or the solver's padded rows (--kernel-layout); L2 flushed before
+    every timed launch."""
     import torch
 
     from paper_2108_08730_gb300 import binding as B
@@ -693,13 +704,22 @@ def run_kernel(args):
     vd = torch.from_numpy(wl.v).cuda()
     R = args.kernel_nrhs
     dt = torch.complex64 if args.kernel_prec == 32 else torch.complex128
-    x = torch.randn((R,) + wl.shape, dtype=dt, device="cuda")
+    padded = args.kernel_layout == "padded"
+    if padded and args.kernel_prec != 32:
+        raise SystemExit("--kernel-layout padded is complex64 only")
+    nz, ny, nx = wl.shape
+    pitch = (nx + 3) // 4 * 4
+    fshape = (R, nz, ny, pitch) if padded else (R,) + wl.shape
+    x = torch.randn(fshape, dtype=dt, device="cuda")
     y = torch.empty_like(x)
-    bb = torch.randn((R,) + wl.shape, dtype=dt, device="cuda") if args.kernel_mode != "apply" else None
+    bb = torch.randn(fshape, dtype=dt, device="cuda") if args.kernel_mode != "apply" else None
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
 
     def launch():
-        if args.kernel_mode == "apply":
+        if padded:
+            ctx.stencil_pitched(g, vd, args.kernel_mode, x, bb, y, pitch,
+                                shift_beta=0.0 if args.kernel_mode == "apply" else 1.0, omega=0.6)
+        elif args.kernel_mode == "apply":
             ctx.apply(g, vd, x, y)
         else:
             ctx.sweep(g, vd, args.kernel_mode, x, bb, y, shift_beta=1.0, omega=0.6)
@@ -732,6 +752,7 @@ def run_kernel(args):
         peaks = _peaks()
         peak = peaks["hbm_gbs"] if peaks else 6800.0
         print(json.dumps({"kernel": f"{args.kernel_mode} fp{args.kernel_prec}", "workload": wl.name,
+                          "layout": args.kernel_layout + (f" (pitch {pitch})" if padded else ""),
                           "nrhs": R, "cfg": cfg if cfg >= 0 else args.kernel_cfg,
                           "points": wl.n_points, "ms": round(ms, 4),
                           "Gpoint_rhs_per_s": round(wl.n_points * R / ms / 1e6, 3),

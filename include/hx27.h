@@ -431,6 +431,13 @@ typedef struct {
                             the coarse correction on the levels below the fine
                             one (the fine level keeps nu_pre / nu_post); 0:
                             nu_pre / nu_post on every level                     */
+  double bicg_kappa;     /* BiCGStab's omega safeguard (Sleijpen and van der
+                            Vorst, 1995): where |cos| of the angle between t and
+                            s is below kappa, omega = (t, s) / (t, t) is scaled
+                            by kappa / |cos|, which keeps the minimal-residual
+                            step from stalling the Bi-CG part on strongly
+                            complex spectra.  0 (default) disables; 0.7 is the
+                            published choice; must be in [0, 1)              */
 } hx_solve_opts;
 
 typedef struct {

@@ -84,7 +84,10 @@ struct SolverImpl : Solver {
   double *tt, *rn2, *bn2, *scale;
   int *active, *brk;
   unsigned* count;                      // arrival counters of the reductions
-  BicgScalars scalars() const { return BicgScalars{rho, rho_new, alpha, omega, beta, rv, ts, tt, rn2, active, brk, count}; }
+  double kappa = 0;
+  BicgScalars scalars() const {
+    return BicgScalars{rho, rho_new, alpha, omega, beta, rv, ts, tt, rn2, active, brk, count, kappa};
+  }
   // pinned host mirrors read at convergence checks
   double* pin_rn2 = nullptr;
   int* pin_act = nullptr;
@@ -473,6 +476,7 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->time_limit_s = 0.0;
   o->cancel = nullptr;
   o->nu_coarse = 2;
+  o->bicg_kappa = 0.0;
 }
 
 namespace {
@@ -656,6 +660,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       opt.check_every < 1 || opt.coarse_galerkin < 0 || opt.coarse_galerkin > 1 ||
       !std::isfinite(opt.pml_cap) || opt.use_graphs < 0 || opt.use_graphs > 1 ||
       opt.autotune < 0 || opt.autotune > 1 || !(opt.time_limit_s >= 0) || opt.mg_levels < 0 || opt.nu_coarse < 0 ||
+      !(opt.bicg_kappa >= 0 && opt.bicg_kappa < 1) ||
       opt.mg_levels > kMaxLev)
     return finish(fail(ctx, HX_ERR_ARG, "invalid solve options"));
   std::vector<int> has_src(nrhs, 0);
@@ -835,6 +840,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
   }
   // Galerkin coarse operators R A P of the shifted operator (inner precision)
   S->galerkin = opt.coarse_galerkin != 0 && S->nlev > 1;
+  S->kappa = opt.bicg_kappa;
   if (S->galerkin) {
     const size_t cs = prec == 64 ? 16 : 8;
     for (int l = 1; l < S->nlev; ++l) {

@@ -260,10 +260,21 @@ __device__ void alpha_step(const BicgScalars& sc, int r) {
   sc.alpha[r] = cdiv(sc.rho[r], sc.rv[r]);
 }
 
-__device__ void omega_step(const BicgScalars& sc, int r) {
+// omega = (t, s) / (t, t); with the safeguard kappa > 0, where the cosine
+// |(t, s)| / (|t| |s|) is below kappa omega is scaled by kappa / cosine
+// (Sleijpen and van der Vorst 1995).  ss = (s, s).
+__device__ void omega_step(const BicgScalars& sc, int r, double ss) {
   if (!sc.active[r]) { sc.omega[r] = make_double2(0, 0); return; }
   if (!(sc.tt[r] > 1e-300)) { sc.omega[r] = make_double2(0, 0); sc.active[r] = 0; sc.brk[r] = 1; return; }
-  sc.omega[r] = make_double2(sc.ts[r].x / sc.tt[r], sc.ts[r].y / sc.tt[r]);
+  double2 om = make_double2(sc.ts[r].x / sc.tt[r], sc.ts[r].y / sc.tt[r]);
+  if (sc.kappa > 0 && ss > 1e-300) {
+    const double cs = sqrt(sc.ts[r].x * sc.ts[r].x + sc.ts[r].y * sc.ts[r].y) / sqrt(sc.tt[r] * ss);
+    if (cs < sc.kappa && cs > 0) {
+      const double g = sc.kappa / cs;
+      om = make_double2(om.x * g, om.y * g);
+    }
+  }
+  sc.omega[r] = om;
 }
 
 // sum of nblk partials in block order (the same order as dot_finish)
@@ -302,7 +313,7 @@ __device__ void reduce_tail(double2 t, double2 q, double2* part, const BicgScala
     sc.count[r] = 0;
     if (KIND == kRedBeta || KIND == kRedBetaNorm) { sc.rho_new[r] = f; beta_step(sc, r); }
     if (KIND == kRedAlpha) { sc.rv[r] = f; alpha_step(sc, r); }
-    if (KIND == kRedOmega) { sc.ts[r] = f; sc.tt[r] = g.x; omega_step(sc, r); }
+    if (KIND == kRedOmega) { sc.ts[r] = f; sc.tt[r] = g.x; omega_step(sc, r, g.y); }
     if (KIND == kRedNorm) sc.rn2[r] = f.x;
     if (KIND == kRedBetaNorm) sc.rn2[r] = g.x;
   }
@@ -319,7 +330,7 @@ bicg_reduce_k(const typename CT<T>::type* __restrict__ a, const typename CT<T>::
   const int r = blockIdx.y;
   const C* ar = a + (long long)r * N;
   const C* br = b + (long long)r * N;
-  T sx = 0, sy = 0, qx = 0;
+  T sx = 0, sy = 0, qx = 0, qy = 0;
   for (long long i = blockIdx.x * (long long)kThreads + threadIdx.x; i < N;
        i += (long long)gridDim.x * kThreads) {
     const C u = ar[i];
@@ -329,12 +340,15 @@ bicg_reduce_k(const typename CT<T>::type* __restrict__ a, const typename CT<T>::
       const C w = br[i];
       sx = fma(u.x, w.x, fma(u.y, w.y, sx));     // Re(conj(u) w)
       sy = fma(u.x, w.y, fma(-u.y, w.x, sy));    // Im(conj(u) w)
-      if (KIND == kRedOmega) qx = fma(u.x, u.x, fma(u.y, u.y, qx));
+      if (KIND == kRedOmega) {
+        qx = fma(u.x, u.x, fma(u.y, u.y, qx));   // (t, t)
+        qy = fma(w.x, w.x, fma(w.y, w.y, qy));   // (s, s)
+      }
     }
   }
   const double2 t = block_sum(make_double2((double)sx, (double)sy));
   double2 q = make_double2(0.0, 0.0);
-  if (KIND == kRedOmega) q = block_sum(make_double2((double)qx, 0.0));
+  if (KIND == kRedOmega) q = block_sum(make_double2((double)qx, (double)qy));
   reduce_tail<KIND>(t, q, part, sc);
 }
 

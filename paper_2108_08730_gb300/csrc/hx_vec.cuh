@@ -80,6 +80,7 @@ struct BicgScalars {
   double *tt, *rn2;
   int *active, *brk;
   unsigned* count;   // R arrival counters, zero between launches
+  double kappa;      // omega safeguard (0: plain minimal-residual omega)
 };
 enum { kRedBeta = 0, kRedAlpha = 1, kRedOmega = 2, kRedNorm = 3, kRedBetaNorm = 4 };
 // partials: >= 2 * R * reduce_blocks(N) double2; b is unused for kRedNorm

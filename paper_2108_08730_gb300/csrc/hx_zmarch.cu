@@ -239,18 +239,29 @@ cudaError_t launch_zmarch(const OpDesc<float>& op, int mode, int cfg, const void
   }
   P.zchunk = best;
   P.nzc = (op.nz + best - 1) / best;
-  // frame kernel: short z-ranges per thread, so its threads fill the GPU
-  // (about 2^19 of them when the frame allows) while each still forms a row's
-  // coefficients once for all the RHS of its block
+  // frame kernel: one thread per (column, z-range, RHS) marching up its
+  // column; z-range length by the same waves x (planes + halo) cost against
+  // its resident CTAs (three 128-thread CTAs per SM: registers)
   {
-    const long long want = 1LL << 19;
-    const long long per_z = std::max<long long>(1, P.fcols * P.nrb);
-    int fz = (int)std::max<long long>(2, std::min<long long>(16, per_z * op.nz / want));
-    if (fz > op.nz) fz = op.nz;
-    P.fzchunk = fz;
-    P.fnzc = (op.nz + fz - 1) / fz;
+    const long long fslots = (long long)num_sms() * 3;
+    const long long per_z = (long long)P.nfc * nrhs;
+    int fbest = op.nz;
+    double fcost = 1e300;
+    for (int fz = op.nz; fz >= 1 && per_z > 0; --fz) {
+      const long long nzc = (op.nz + fz - 1) / fz;
+      if ((op.nz + nzc - 1) / nzc != fz) continue;
+      const long long ctas = per_z * nzc;
+      if (ctas > (1LL << 30)) break;
+      const double cost = (double)((ctas + fslots - 1) / fslots) * (fz + 2);
+      if (cost < fcost * 0.999) {
+        fcost = cost;
+        fbest = fz;
+      }
+    }
+    P.fzchunk = fbest;
+    P.fnzc = (op.nz + fbest - 1) / fbest;
   }
-  const long long nframe = (long long)P.nfc * P.fnzc * P.nrb;
+  const long long nframe = (long long)P.nfc * P.fnzc * nrhs;
   const long long ninter = (long long)P.ntx * P.nty * P.nzc * P.nrb;
   if (nframe + ninter <= 0) return cudaSuccess;
   if (nframe > (1LL << 31) - 1 || ninter > (1LL << 31) - 1) return cudaErrorInvalidConfiguration;

@@ -26,11 +26,11 @@
 //    3-plane window of sums; that is what lets 8 RHS share a CTA's row
 //    coefficients.
 //  * A second kernel, launched first, takes the rows in the x/y PML (the
-//    "frame"), one thread per (column, z-range, RHS block), in the general
-//    factored form (27 neighbours through the read-only cache); packed
-//    densely, so no lane of a 32-wide tile idles on a 10-node PML band, and
-//    with no shared memory, so it runs at high occupancy on its own register
-//    budget.
+//    "frame"), one thread per (column, z-range, RHS), in the general factored
+//    form: the thread marches up its column with three planes' 3 x 3
+//    neighbourhoods in registers and the next one in flight; columns are
+//    packed densely, so no lane of a 32-wide tile idles on a 10-node PML
+//    band, and it uses no shared memory.
 //  * Packed FP32x2 arithmetic (__fadd2_rn / __ffma2_rn) for complex values
 //    times real coefficients.
 //  * Every wait on an mbarrier is bounded (about one second of globaltimer);
@@ -85,7 +85,7 @@ struct ZParams {
   int xs, ys, ntx, nty;     // interior tiles: origin (xs even) and counts
   int xlo, xhi, ylo, yhi;   // rows with no x/y stretching: [xlo, xhi] x [ylo, yhi] (may be empty)
   long long fcols;          // frame columns (x or y in the PML)
-  int nfc;                  // frame-kernel CTAs per (frame z-chunk, RHS block)
+  int nfc;                  // frame-kernel CTAs per (frame z-chunk, RHS)
   int fzchunk, fnzc;        // frame kernel: planes per thread, z-chunks
   float omega_j;
   int* err;
@@ -443,30 +443,66 @@ __device__ __forceinline__ void frame_column(const ZParams& P, long long c, int&
 
 // General row (any stretching): sum_d up_d (F_d+ - F_d0) + dn_d (F_d- - F_d0)
 // + m (1 + i beta) mass, F_d the transverse averages (t0, t1, t2) of the
-// planes normal to d, neighbours read plane by plane through the read-only
-// cache.
-template <int MODE, int RB, bool SHIFT>
+// planes normal to d.  One thread per (frame column, z-range, RHS): it marches
+// up its column with the 3 x 3 neighbourhoods of planes z - 1, z, z + 1 in
+// registers while plane z + 2 is in flight, so each plane is read once per
+// column instead of once per row it feeds.  Neighbourhood element 3 dj + di is
+// (ix + di - 1, iy + dj - 1); out-of-grid elements are zero.
+template <int MODE, bool SHIFT>
 __device__ __forceinline__ void frame(const ZParams& P, int fcta) {
   const OpDesc<float>& op = P.op;
   int t = fcta;
-  const int rblk = t % P.nrb;
-  t /= P.nrb;
+  const int r = t % P.nrhs;
+  t /= P.nrhs;
   const int zc = t % P.fnzc;
   const long long c = (long long)(t / P.fnzc) * kZFrameThreads + threadIdx.x;
   if (c >= P.fcols) return;
   int ix, iy;
   frame_column(P, c, ix, iy);
   const int nx = op.nx, ny = op.ny, nz = op.nz;
-  const int r0 = rblk * RB, rcount = min(RB, P.nrhs - r0);
   const int z0 = zc * P.fzchunk, z1 = min(nz, z0 + P.fzchunk);
   const bool has_b = MODE != kApply && P.b != nullptr;
   const float4 ax = ldg4(op.axis[0] + 4 * (size_t)ix), ay = ldg4(op.axis[1] + 4 * (size_t)iy);
-  const bool xm = ix > 0, xp = ix < nx - 1, ym = iy > 0, yp = iy < ny - 1;
-  const long long col = (long long)iy * P.pitch + ix;
+  unsigned in9 = 0;   // bit 3 dj + di: that neighbour lies inside the grid
+#pragma unroll
+  for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+    for (int di = 0; di < 3; ++di)
+      if ((dj != 0 || iy > 0) && (dj != 2 || iy < ny - 1) && (di != 0 || ix > 0) && (di != 2 || ix < nx - 1))
+        in9 |= 1u << (3 * dj + di);
+  const long long roff = (long long)r * P.rstride + (long long)iy * P.pitch + ix;
+  const float* vc = op.v + (long long)iy * nx + ix;
   const long long vplane = (long long)nx * ny;
-#pragma unroll 1
-  for (int z = z0; z < z1; ++z) {
-    const float iv = rcp_fast(__ldg(op.v + z * vplane + (long long)iy * nx + ix));
+
+  // columns away from the grid's x/y faces read their neighbourhoods unchecked
+  const bool face = in9 != 0x1ffu;
+  auto load = [&](float2(&a)[9], int q) {
+    if (q < 0 || q >= nz) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) a[k] = make_float2(0.f, 0.f);
+      return;
+    }
+    const float2* p = P.x + roff + (long long)q * P.plane;
+    if (!face) {
+#pragma unroll
+      for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+        for (int di = 0; di < 3; ++di) a[3 * dj + di] = __ldg(p + (dj - 1) * P.pitch + (di - 1));
+    } else {
+#pragma unroll
+      for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+        for (int di = 0; di < 3; ++di)
+          a[3 * dj + di] = ((in9 >> (3 * dj + di)) & 1u) ? __ldg(p + (dj - 1) * P.pitch + (di - 1))
+                                                          : make_float2(0.f, 0.f);
+    }
+  };
+
+  // row z from the neighbourhoods of planes z - 1 (Am), z (A0) and z + 1 (Ap)
+  auto row = [&](const float2(&Am)[9], const float2(&A0)[9], const float2(&Ap)[9], int z, float vv) {
+    const long long oo = roff + (long long)z * P.plane;
+    const float2 bz = has_b ? __ldg(P.b + oo) : make_float2(0.f, 0.f);
+    const float iv = rcp_fast(vv);
     const float u = fminf(fmaxf(op.u_scale * iv, 0.f), (float)(op.n_g - 1));
     const int i0 = min((int)u, op.n_g - 2);
     const float tf = u - (float)i0;
@@ -478,82 +514,77 @@ __device__ __forceinline__ void frame(const ZParams& P, int fcta) {
     const float t0 = lerp(tf, lt.x, ht.x), t1 = lerp(tf, lt.y, ht.y), t2 = lerp(tf, lt.z, ht.z);
     const float4 az = ldg4(op.axis[2] + 4 * (size_t)z);
     const float2 mc = make_float2(m, SHIFT ? op.beta * m : 0.f);
-    const bool zin[3] = {z > 0, true, z < nz - 1};
-    float2 dinv = make_float2(0.f, 0.f);
+    float2 Fx[3], Fy[3], Fz[3];
+    float2 ms = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) Fx[i] = Fy[i] = ms;
+    auto plane = [&](const float2(&a)[9], int dk) {
+      // weights of this plane in the transverse averages normal to x and y
+      const float2 Ta = dup(dk == 1 ? t0 : t1), Tb = dup(dk == 1 ? t1 : t2);
+      float2 vs[3], hs[3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        vs[i] = f2add(a[i], a[6 + i]);           // column i: y-neighbours
+        hs[i] = f2add(a[3 * i], a[3 * i + 2]);   // row i: x-neighbours
+      }
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        Fx[i] = f2fma(Tb, vs[i], f2fma(Ta, a[3 + i], Fx[i]));
+        Fy[i] = f2fma(Tb, hs[i], f2fma(Ta, a[3 * i + 1], Fy[i]));
+      }
+      const float2 faces = f2add(hs[1], vs[1]), corners = f2add(vs[0], vs[2]);
+      Fz[dk] = f2fma(dup(t2), corners, f2fma(dup(t1), faces, f2mul(dup(t0), a[4])));
+      // consistent mass (second form of Eq. 8): centre / faces / edges / corners
+      const float m0 = dk == 1 ? w1 : w2, m1 = dk == 1 ? w2 : w3, m2 = dk == 1 ? w3 : w4;
+      ms = f2fma(dup(m2), corners, f2fma(dup(m1), faces, f2fma(dup(m0), a[4], ms)));
+    };
+    plane(Am, 0);
+    plane(A0, 1);
+    plane(Ap, 2);
+    float2 acc = cmul(mc, ms);
+    acc = cmac(make_float2(ax.x, ax.y), Fx[2], cmac(make_float2(ax.z, ax.w), Fx[0],
+               cmac(make_float2(-(ax.x + ax.z), -(ax.y + ax.w)), Fx[1], acc)));
+    acc = cmac(make_float2(ay.x, ay.y), Fy[2], cmac(make_float2(ay.z, ay.w), Fy[0],
+               cmac(make_float2(-(ay.x + ay.z), -(ay.y + ay.w)), Fy[1], acc)));
+    acc = cmac(make_float2(az.x, az.y), Fz[2], cmac(make_float2(az.z, az.w), Fz[0],
+               cmac(make_float2(-(az.x + az.z), -(az.y + az.w)), Fz[1], acc)));
+    float2 res = acc;
+    if (MODE == kResidual) res = f2sub(bz, acc);
     if (MODE == kJacobi) {
       const float sdx = ax.x + ax.z + ay.x + ay.z + az.x + az.z;
       const float sdy = ax.y + ax.w + ay.y + ay.w + az.y + az.w;
-      dinv = crcp(make_float2(fmaf(mc.x, w1, -t0 * sdx), fmaf(mc.y, w1, -t0 * sdy)));
+      float2 dinv = crcp(make_float2(fmaf(mc.x, w1, -t0 * sdx), fmaf(mc.y, w1, -t0 * sdy)));
       dinv = make_float2(P.omega_j * dinv.x, P.omega_j * dinv.y);
+      res = cmac(dinv, f2sub(bz, acc), A0[4]);
     }
-    const long long o = (long long)z * P.plane + col;
-    // rows away from the grid's faces read their 27 neighbours unchecked
-    const bool edge = !(xm && xp && ym && yp && zin[0] && zin[2]);
+    P.y[oo] = res;
+  };
+
+  // the window rotates through four register sets: (W0, W1, W2) hold planes
+  // z - 1, z, z + 1 while plane z + 2 is loaded into W3, and so on
+  float2 W0[9], W1[9], W2[9], W3[9];
+  load(W0, z0 - 1);
+  load(W1, z0);
+  load(W2, z0 + 1);
+  float vv = __ldg(vc + z0 * vplane);
+  auto it = [&](float2(&Am)[9], float2(&A0)[9], float2(&Ap)[9], float2(&An)[9], int z) {
+    float vn = 1500.f;
+    if (z + 1 < z1) {
+      load(An, z + 2);
+      vn = __ldg(vc + (z + 1) * vplane);
+    }
+    row(Am, A0, Ap, z, vv);
+    vv = vn;
+  };
 #pragma unroll 1
-    for (int r = 0; r < rcount; ++r) {
-      const float2* xr = P.x + (long long)(r0 + r) * P.rstride + o;
-      float2 Fx[3], Fy[3], Fz[3];
-      float2 ms = make_float2(0.f, 0.f), xc = ms;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) Fx[i] = Fy[i] = ms;
-#pragma unroll
-      for (int dk = 0; dk < 3; ++dk) {
-        // plane z + dk - 1: 3 x 3 values a[dy][dx] (zero outside the grid)
-        float2 a[3][3];
-        const float2* xp_ = xr + (dk - 1) * P.plane;
-        if (!edge) {
-#pragma unroll
-          for (int dj = 0; dj < 3; ++dj) {
-            const float2* row = xp_ + (dj - 1) * P.pitch;
-#pragma unroll
-            for (int di = 0; di < 3; ++di) a[dj][di] = __ldg(row + (di - 1));
-          }
-        } else {
-#pragma unroll
-          for (int dj = 0; dj < 3; ++dj)
-#pragma unroll
-            for (int di = 0; di < 3; ++di) {
-              const bool in = zin[dk] && (dj != 0 || ym) && (dj != 2 || yp) && (di != 0 || xm) && (di != 2 || xp);
-              a[dj][di] = in ? __ldg(xp_ + (dj - 1) * P.pitch + (di - 1)) : make_float2(0.f, 0.f);
-            }
-        }
-        // weights of this plane in the transverse averages normal to x and y
-        const float2 Ta = dup(dk == 1 ? t0 : t1), Tb = dup(dk == 1 ? t1 : t2);
-        float2 vs[3], hs[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          vs[i] = f2add(a[0][i], a[2][i]);   // column i: y-neighbours
-          hs[i] = f2add(a[i][0], a[i][2]);   // row i: x-neighbours
-        }
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          Fx[i] = f2fma(Tb, vs[i], f2fma(Ta, a[1][i], Fx[i]));
-          Fy[i] = f2fma(Tb, hs[i], f2fma(Ta, a[i][1], Fy[i]));
-        }
-        const float2 faces = f2add(hs[1], vs[1]), corners = f2add(vs[0], vs[2]);
-        Fz[dk] = f2fma(dup(t2), corners, f2fma(dup(t1), faces, f2mul(dup(t0), a[1][1])));
-        // consistent mass (second form of Eq. 8): centre / faces / edges / corners
-        const float m0 = dk == 1 ? w1 : w2, m1 = dk == 1 ? w2 : w3, m2 = dk == 1 ? w3 : w4;
-        ms = f2fma(dup(m2), corners, f2fma(dup(m1), faces, f2fma(dup(m0), a[1][1], ms)));
-        if (dk == 1) xc = a[1][1];
-        sched_fence();
-      }
-      float2 acc = cmul(mc, ms);
-      acc = cmac(make_float2(ax.x, ax.y), Fx[2], cmac(make_float2(ax.z, ax.w), Fx[0],
-                 cmac(make_float2(-(ax.x + ax.z), -(ax.y + ax.w)), Fx[1], acc)));
-      acc = cmac(make_float2(ay.x, ay.y), Fy[2], cmac(make_float2(ay.z, ay.w), Fy[0],
-                 cmac(make_float2(-(ay.x + ay.z), -(ay.y + ay.w)), Fy[1], acc)));
-      acc = cmac(make_float2(az.x, az.y), Fz[2], cmac(make_float2(az.z, az.w), Fz[0],
-                 cmac(make_float2(-(az.x + az.z), -(az.y + az.w)), Fz[1], acc)));
-      const long long oo = (long long)(r0 + r) * P.rstride + o;
-      float2 res = acc;
-      if (MODE == kResidual) res = has_b ? f2sub(__ldg(P.b + oo), acc) : make_float2(-acc.x, -acc.y);
-      if (MODE == kJacobi) {
-        const float2 rr = has_b ? f2sub(__ldg(P.b + oo), acc) : make_float2(-acc.x, -acc.y);
-        res = cmac(dinv, rr, xc);
-      }
-      P.y[oo] = res;
-    }
+  for (int z = z0; z < z1; z += 4) {
+    it(W0, W1, W2, W3, z);
+    if (z + 1 >= z1) break;
+    it(W1, W2, W3, W0, z + 1);
+    if (z + 2 >= z1) break;
+    it(W2, W3, W0, W1, z + 2);
+    if (z + 3 >= z1) break;
+    it(W3, W0, W1, W2, z + 3);
   }
 }
 
@@ -561,10 +592,10 @@ __device__ __forceinline__ void frame(const ZParams& P, int fcta) {
 // at high occupancy with their own register budget), then the interior tiles.
 // They write disjoint rows; the interior kernel is launched after the frame
 // kernel on the same stream (dependent launch hides the gap).
-template <int MODE, int RB, bool SHIFT>
-__global__ void __launch_bounds__(kZFrameThreads, 4) zm_frame_kernel(const ZParams P) {
+template <int MODE, bool SHIFT>
+__global__ void __launch_bounds__(kZFrameThreads, 3) zm_frame_kernel(const ZParams P) {
   pdl_enter();
-  frame<MODE, RB, SHIFT>(P, blockIdx.x);
+  frame<MODE, SHIFT>(P, blockIdx.x);
 }
 
 template <int MODE, int TY, int RB, bool SHIFT>
@@ -585,7 +616,7 @@ cudaError_t zm_launch_mode(const ZParams& P, bool shift, const CUtensorMap& xmap
                            int frame, int interior, cudaStream_t s) {
   using K = ZK<TY, RB, MODE != kApply>;
   if (frame > 0) {
-    auto fk = shift ? zm::zm_frame_kernel<MODE, RB, true> : zm::zm_frame_kernel<MODE, RB, false>;
+    auto fk = shift ? zm::zm_frame_kernel<MODE, true> : zm::zm_frame_kernel<MODE, false>;
     cudaError_t e = launch_k(fk, dim3((unsigned)frame), dim3(kZFrameThreads), 0, s, P);
     count_launch(1);
     if (e != cudaSuccess) return e;
