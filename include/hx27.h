@@ -436,8 +436,12 @@ typedef struct {
                             s is below kappa, omega = (t, s) / (t, t) is scaled
                             by kappa / |cos|, which keeps the minimal-residual
                             step from stalling the Bi-CG part on strongly
-                            complex spectra.  0 (default) disables; 0.7 is the
-                            published choice; must be in [0, 1)              */
+                            complex spectra.  Default 0.7 (the published
+                            choice); 0 disables; must be in [0, 1)           */
+  int coarse_velocity;   /* the preconditioner's coarse-level velocity, from the
+                            next finer level: 0 (default) injection (the fine
+                            node under the coarse one); 1 the full-weighting
+                            average of 1/v^2 over its 27 fine neighbours      */
 } hx_solve_opts;
 
 typedef struct {

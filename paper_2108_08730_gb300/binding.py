@@ -64,7 +64,7 @@ class hx_solve_opts(C.Structure):
                 ("source_spread", C.c_int), ("initial_guess", C.c_int), ("check_every", C.c_int),
                 ("coarse_galerkin", C.c_int), ("pml_cap", C.c_double), ("use_graphs", C.c_int),
                 ("autotune", C.c_int), ("time_limit_s", C.c_double), ("cancel", C.c_void_p),
-                ("nu_coarse", C.c_int), ("bicg_kappa", C.c_double)]
+                ("nu_coarse", C.c_int), ("bicg_kappa", C.c_double), ("coarse_velocity", C.c_int)]
 
 
 class hx_solve_report(C.Structure):

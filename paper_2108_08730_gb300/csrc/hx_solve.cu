@@ -476,7 +476,8 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->time_limit_s = 0.0;
   o->cancel = nullptr;
   o->nu_coarse = 2;
-  o->bicg_kappa = 0.0;
+  o->bicg_kappa = 0.7;
+  o->coarse_velocity = 0;
 }
 
 namespace {
@@ -660,7 +661,7 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       opt.check_every < 1 || opt.coarse_galerkin < 0 || opt.coarse_galerkin > 1 ||
       !std::isfinite(opt.pml_cap) || opt.use_graphs < 0 || opt.use_graphs > 1 ||
       opt.autotune < 0 || opt.autotune > 1 || !(opt.time_limit_s >= 0) || opt.mg_levels < 0 || opt.nu_coarse < 0 ||
-      !(opt.bicg_kappa >= 0 && opt.bicg_kappa < 1) ||
+      !(opt.bicg_kappa >= 0 && opt.bicg_kappa < 1) || opt.coarse_velocity < 0 || opt.coarse_velocity > 1 ||
       opt.mg_levels > kMaxLev)
     return finish(fail(ctx, HX_ERR_ARG, "invalid solve options"));
   std::vector<int> has_src(nrhs, 0);
@@ -832,11 +833,12 @@ extern "C" int hx_solve(hx_ctx* ctx, const hx_grid* grid, const float* v_dev, co
       if ((st = own_copy(S->n[l], grid->h * (double)(1 << l), pml_cap, &S->lvl[l]))) return finish(st);
     S->op_key = okey;
   }
-  // coarse velocities by injection
+  // coarse velocities, level by level (injection or averaged slowness squared)
   for (int l = 1; l < S->nlev; ++l) {
     const float* vf = l == 1 ? v_dev : (const float*)S->vlev[l - 1].p;
-    cudaError_t e = launch_inject_velocity(vf, S->n[l - 1], (float*)S->vlev[l].p, S->n[l], stream);
-    if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "velocity injection"));
+    cudaError_t e = launch_coarse_velocity(vf, S->n[l - 1], (float*)S->vlev[l].p, S->n[l], opt.coarse_velocity,
+                                           stream);
+    if (e != cudaSuccess) return finish(cuda_fail(ctx, e, "coarse velocity"));
   }
   // Galerkin coarse operators R A P of the shifted operator (inner precision)
   S->galerkin = opt.coarse_galerkin != 0 && S->nlev > 1;

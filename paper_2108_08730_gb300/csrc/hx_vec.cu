@@ -196,6 +196,41 @@ __global__ void inject_v_k(const float* __restrict__ vf, int fx, int fy, float* 
   }
 }
 
+// Coarse velocity from the full-weighting average (1/4, 1/2, 1/4 per axis,
+// renormalised at the grid's faces) of the slowness squared 1/v^2 around the
+// fine node 2X: the coefficient of the mass term, so a coarse node sees the
+// bodies its neighbourhood holds instead of one sample of them.
+__global__ void coarsen_slowness_k(const float* __restrict__ vf, int fx, int fy, int fz, float* __restrict__ vc,
+                                   int cx, int cy, int cz) {
+  pdl_enter();
+  const long long Nc = (long long)cx * cy * cz;
+  for (long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x; I < Nc;
+       I += (long long)gridDim.x * blockDim.x) {
+    const int X = (int)(I % cx), Y = (int)((I / cx) % cy), Z = (int)(I / ((long long)cx * cy));
+    float acc = 0.f, wsum = 0.f;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int z = 2 * Z + dz;
+      if (z < 0 || z >= fz) continue;
+      const float wz = dz == 0 ? 0.5f : 0.25f;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int y = 2 * Y + dy;
+        if (y < 0 || y >= fy) continue;
+        const float wy = wz * (dy == 0 ? 0.5f : 0.25f);
+        const float* row = vf + ((long long)z * fy + y) * fx;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int x = 2 * X + dx;
+          if (x < 0 || x >= fx) continue;
+          const float w = wy * (dx == 0 ? 0.5f : 0.25f);
+          const float sl = 1.f / row[x];
+          acc = fmaf(w, sl * sl, acc);
+          wsum += w;
+        }
+      }
+    }
+    vc[I] = rsqrtf(acc / wsum);
+  }
+}
+
 // The complex64 side may use a padded x-row pitch p32 (rows of nx points);
 // the complex128 side is unpadded.  Padding is neither read nor written.
 __global__ void cast_scale_k(const double2* __restrict__ r64, float2* __restrict__ r32,
@@ -475,10 +510,14 @@ cudaError_t launch_prolong_add(void* fine, const int nf[3], const void* coarse, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_inject_velocity(const float* vf, const int nf[3], float* vc, const int nc[3],
+cudaError_t launch_coarse_velocity(const float* vf, const int nf[3], float* vc, const int nc[3], int mode,
                                    cudaStream_t s) {
   const long long Nc = (long long)nc[0] * nc[1] * nc[2];
-  (void)launch_k(inject_v_k, grid_for(Nc, 1, 1), kThreads, 0, s, vf, nf[0], nf[1], vc, nc[0], nc[1], nc[2]);
+  if (mode == 1)
+    (void)launch_k(coarsen_slowness_k, grid_for(Nc, 1, 1), kThreads, 0, s, vf, nf[0], nf[1], nf[2], vc, nc[0],
+                   nc[1], nc[2]);
+  else
+    (void)launch_k(inject_v_k, grid_for(Nc, 1, 1), kThreads, 0, s, vf, nf[0], nf[1], vc, nc[0], nc[1], nc[2]);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -34,7 +34,9 @@ cudaError_t launch_restrict(const void* fine, const int nf[3], void* coarse, con
 template <typename T>
 cudaError_t launch_prolong_add(void* fine, const int nf[3], const void* coarse, const int nc[3],
                                int R, cudaStream_t s, long long fpitch = 0);
-cudaError_t launch_inject_velocity(const float* vf, const int nf[3], float* vc, const int nc[3],
+// Coarse-level velocity from the next finer level (coarse node X over fine
+// node 2X): mode 0 injection, mode 1 full-weighting average of 1/v^2.
+cudaError_t launch_coarse_velocity(const float* vf, const int nf[3], float* vc, const int nc[3], int mode,
                                    cudaStream_t s);
 
 // r32[r,i] = (complex64)(r64[r,i] * scale[r]);  x64[r,i] += scale[r] * d32[r,i]

@@ -111,6 +111,25 @@ def test_batch_invariance(ctx, otable):
         assert M.rel_l2(alone[0], batch[k]) <= 1e-9
 
 
+@pytest.mark.parametrize("opts", [{"bicg_kappa": 0.0}, {"bicg_kappa": 0.5}, {"coarse_velocity": 1}])
+def test_solver_options_reach_the_oracle_residual(ctx, otable, opts):
+    # The omega safeguard and the averaged coarse velocity change only the
+    # iterates: on a small sharp-contrast model (bodies and lens) the wavefield
+    # must meet the oracle's FP64 CSR residual and agree with the default solve.
+    wl = synth.sharp_contrast(40, 36, 32, 25.0, 7.0, 5, seed=79, n_src_side=2)   # 44 % at 4500, 52 % lens
+    src = B.sources_of(wl)
+    ref, _ = _gpu_solve(ctx, wl, src, tol=1e-11)
+    got, rep = _gpu_solve(ctx, wl, src, tol=1e-11, **opts)
+    assert rep["status"] == 0
+    nodes, T = otable
+    prof = O.profiles_for(wl.shape, wl.h, wl.npml, wl.v_ref, wl.r_coef)
+    A = O.assemble_csr(wl.v, wl.h, wl.f, prof, T, nodes)
+    for r, (ix, iy, iz) in enumerate(wl.sources):
+        s = S.point_sources(wl.shape, wl.h, [(ix, iy, iz)]).reshape(-1)
+        assert S.relative_residual(A, got[r].reshape(-1), s) <= 1e-10
+    assert M.rel_l2(got, ref) <= 1e-6
+
+
 def test_solve_argument_errors(ctx):
     wl = synth.homogeneous()
     g = B.grid_of(wl)
@@ -128,6 +147,10 @@ def test_solve_argument_errors(ctx):
     with pytest.raises(B.HxError) as e:
         ctx.solve(g, vslow, B.sources_of(wl), 1, out)
     assert e.value.code == -1
+    for bad in ({"bicg_kappa": 1.0}, {"bicg_kappa": -0.1}, {"coarse_velocity": 2}):
+        with pytest.raises(B.HxError) as e:
+            ctx.solve(g, v, B.sources_of(wl), 1, out, **bad)
+        assert e.value.code == -1
     c2 = B.Context(0)                                             # no table yet
     with pytest.raises(B.HxError) as e:
         c2.solve(g, v, B.sources_of(wl), 1, out)
