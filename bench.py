@@ -56,6 +56,12 @@ UNIT = "Mpoint*RHS/s"
 # (1/v, the lerp of 11 table entries, the class coefficients: about 40).
 FP64_FLOPS_PER_POINT_RHS = 68
 FP64_FLOPS_PER_POINT = 40
+# Serving leg: the admission's bound on how long a large request is passed
+# over, the omega safeguard of the served solves, and the longest span of the
+# Poisson arrivals.
+SERVE_MAX_WAIT_S = 120.0
+SERVE_KAPPA = 0.7
+SERVE_MAX_SPAN_S = 600.0
 
 
 def _args():
@@ -578,7 +584,9 @@ def run_serving(args, T, nreq=None, seed0=5000, log=None):
     (model family uniform over the four synthetic families, sides
     log-uniform in 64..256, f ~ U(2, 10) Hz, 1..32 sources, h = 25 m, 8-node
     PML), Poisson arrivals at a rate giving an offered load of 0.8 x the solo
-    capacity measured on the first requests solved one at a time.  Returns the
+    capacity measured on the first requests solved one at a time (faster when
+    that would spread the arrivals over more than SERVE_MAX_SPAN_S), admitted
+    smallest first.  Returns the
     serving summary (latency percentiles from submission to wavefield on the
     host, point*RHS/s over the busy interval)."""
     import numpy as np
@@ -589,12 +597,15 @@ def run_serving(args, T, nreq=None, seed0=5000, log=None):
     nreq = args.serve_requests if nreq is None else nreq
     reqs = [synth.serving_request(seed0 + k) for k in range(nreq)]
     work = np.array([r.n_points * r.nrhs for r in reqs], dtype=np.float64)
-    srv = B.Server(T, slots=args.serve_slots)
+    # smallest request first (a request that has waited SERVE_MAX_WAIT_S goes
+    # first), and the BiCGStab omega safeguard, which removes the stalls of the
+    # strongly heterogeneous requests
+    srv = B.Server(T, slots=args.serve_slots, order="smallest", max_wait_s=SERVE_MAX_WAIT_S)
 
     def submit(k, wl, limit):
         out = np.zeros((wl.nrhs,) + wl.shape, dtype=np.complex128)
         t = srv.submit(B.grid_of(wl), wl.v, B.sources_of(wl), wl.nrhs, out, model_id=seed0 + k,
-                       time_limit_s=limit)
+                       time_limit_s=limit, bicg_kappa=SERVE_KAPPA)
         return t, out
 
     # solo capacity: the first requests one at a time (also warms the engine)
@@ -606,7 +617,10 @@ def run_serving(args, T, nreq=None, seed0=5000, log=None):
         if r["status"] != 0:
             raise RuntimeError(f"serving calibration request {k} failed: {r}")
     solo = work[:ncal].sum() / (time.perf_counter() - t0)          # point*RHS/s
-    rate = 0.8 * solo / work.mean()                                   # requests/s
+    # offered load 0.8 of the calibrated capacity, the arrivals spread over at
+    # most SERVE_MAX_SPAN_S (bounds the leg's length when the calibration
+    # requests happen to be slow)
+    rate = max(0.8 * solo / work.mean(), nreq / SERVE_MAX_SPAN_S)    # requests/s
     srv.stats(reset=True)
     rng = np.random.default_rng(seed0)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
@@ -635,7 +649,11 @@ def run_serving(args, T, nreq=None, seed0=5000, log=None):
             "deadline_s": f"{args.serve_deadline:g} + {args.serve_slots} x point*RHS / solo capacity "
                           f"({min(limits):.1f} .. {max(limits):.1f} s)",
             "inner_iters_median": float(np.median(iters)), "inner_iters_max": int(max(iters)),
-            "arrival_rate_per_s": round(rate, 4), "offered_load": 0.8,
+            "arrival_rate_per_s": round(rate, 4),
+            "offered_load": round(rate * work.mean() / solo, 3),
+            "admission": f"smallest point*RHS first; a request waiting {SERVE_MAX_WAIT_S:g} s or "
+                         "longer goes first",
+            "solve_options": f"library defaults with bicg_kappa = {SERVE_KAPPA:g}",
             "solo_capacity_mpoint_rhs_s": round(solo / 1e6, 3),
             "p50_ms": round(st["p50_ms"], 2),
             # a 99th percentile needs at least 100 completed requests

@@ -83,7 +83,8 @@ class hx_apply_item(C.Structure):
 
 class hx_server_config(C.Structure):
     _fields_ = [("device", C.c_int), ("slots", C.c_int), ("mem_budget", C.c_double),
-                ("table", C.POINTER(C.c_double)), ("n_g", C.c_int), ("d_inv_g", C.c_double)]
+                ("table", C.POINTER(C.c_double)), ("n_g", C.c_int), ("d_inv_g", C.c_double),
+                ("order", C.c_int), ("max_wait_s", C.c_double)]
 
 
 class hx_request(C.Structure):
@@ -448,10 +449,14 @@ class Server:
     output wavefield (complex128 (nrhs, nz, ny, nx)); both are kept alive
     here until the request has been waited for."""
 
-    def __init__(self, table, device=0, slots=2, mem_budget=0.0, d_inv_g=0.001):
+    def __init__(self, table, device=0, slots=2, mem_budget=0.0, d_inv_g=0.001, order="fifo",
+                 max_wait_s=0.0):
+        """order: "fifo" (first come, first served) or "smallest" (smallest
+        request first; one waiting max_wait_s or longer goes first)."""
         self._T = np.ascontiguousarray(table, dtype=np.float64)
+        o = {"fifo": 0, "smallest": 1}.get(order, -1)
         cfg = hx_server_config(int(device), int(slots), float(mem_budget), _dptr(self._T),
-                               self._T.shape[0], float(d_inv_g))
+                               self._T.shape[0], float(d_inv_g), o, float(max_wait_s))
         h = C.c_void_p()
         st = lib().hx_server_create(C.byref(h), C.byref(cfg))
         if st != HX_OK:

@@ -7,8 +7,10 @@
 // single mutex guards the queue, the admission bookkeeping, the model cache
 // and the results; solves run outside it.
 //
-// Admission: first come, first served.  The request at the head of the queue
-// starts when a worker is free and
+// Admission order (hx_server_config.order): first come, first served, or the
+// smallest request (grid points x RHS) first, where a request that has waited
+// max_wait_s or longer goes ahead of the rest, oldest first.  The selected
+// request (the "head") starts when a worker is free and
 //     estimate(head) + sum over other workers of their committed bytes
 //                    + bytes of resident models <= budget.
 // A worker's committed bytes are the estimate of the request it runs, or of
@@ -85,6 +87,8 @@ double estimate_bytes(const hx_grid& g, int nrhs, int mode) {
 struct hx_server {
   int device = 0;
   double budget = 0;
+  int order = 0;                     // 0: first come, first served; 1: smallest first
+  double max_wait_s = 0;             // order 1: waits this long or longer go first (0: never)
   std::vector<double> table;
   int n_g = 0;
   double d_inv_g = 0;
@@ -109,6 +113,21 @@ struct hx_server {
   int running = 0, max_running = 0;
   bool have_first = false;
   Clock::time_point t_first, t_last;
+
+  // the request admission considers next (queue not empty)
+  std::deque<Pending>::iterator select_head() {
+    if (order == 0) return queue.begin();
+    const auto now = Clock::now();
+    if (max_wait_s > 0 && std::chrono::duration<double>(now - queue.front().t_submit).count() >= max_wait_s)
+      return queue.begin();                      // the queue is in submission order
+    auto work = [](const Pending& p) {
+      return (double)p.req.grid.nx * p.req.grid.ny * p.req.grid.nz * p.req.nrhs;
+    };
+    auto best = queue.begin();
+    for (auto it = queue.begin(); it != queue.end(); ++it)
+      if (work(*it) < work(*best)) best = it;    // ties: the earlier submission
+    return best;
+  }
 
   double committed_except(int w) const {
     double c = model_bytes;
@@ -153,8 +172,9 @@ void hx_server::worker_main(int w) {
   cudaSetDevice(device);
   std::unique_lock<std::mutex> lk(mu);
   for (;;) {
-    // ---- admission of the head of the queue
+    // ---- admission of the selected request
     double need = 0;
+    std::deque<Pending>::iterator sel;
     for (;;) {
       if (W.drop_cache) {
         release_workspace(W);
@@ -166,7 +186,8 @@ void hx_server::worker_main(int w) {
         cv_work.wait(lk);
         continue;
       }
-      const Pending& head = queue.front();
+      sel = select_head();
+      const Pending& head = *sel;
       need = head.est + (models.count(model_key(head.req)) ? 0.0 : model_size(head.req.grid));
       if (committed_except(w) + need <= budget) break;
       evict_models(need, w);
@@ -180,8 +201,8 @@ void hx_server::worker_main(int w) {
       cv_work.notify_all();
       cv_work.wait(lk);
     }
-    Pending p = std::move(queue.front());
-    queue.pop_front();
+    Pending p = std::move(*sel);
+    queue.erase(sel);
     running_flags[p.ticket] = p.cancel;
     W.busy = true;
     W.committed = p.est;
@@ -280,7 +301,8 @@ extern "C" {
 int hx_server_create(hx_server** out, const hx_server_config* cfg) {
   if (!out) return HX_ERR_ARG;
   *out = nullptr;
-  if (!cfg || cfg->slots < 1 || cfg->slots > 64 || !cfg->table || cfg->n_g < 2 || !(cfg->d_inv_g > 0))
+  if (!cfg || cfg->slots < 1 || cfg->slots > 64 || !cfg->table || cfg->n_g < 2 || !(cfg->d_inv_g > 0) ||
+      cfg->order < 0 || cfg->order > 1 || !(cfg->max_wait_s >= 0))
     return HX_ERR_ARG;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return HX_ERR_CUDA;
@@ -291,6 +313,8 @@ int hx_server_create(hx_server** out, const hx_server_config* cfg) {
   srv->table.assign(cfg->table, cfg->table + 7 * (size_t)cfg->n_g);
   srv->n_g = cfg->n_g;
   srv->d_inv_g = cfg->d_inv_g;
+  srv->order = cfg->order;
+  srv->max_wait_s = cfg->max_wait_s;
   size_t freeb = 0, totalb = 0;
   if (cudaMemGetInfo(&freeb, &totalb) != cudaSuccess) {
     delete srv;

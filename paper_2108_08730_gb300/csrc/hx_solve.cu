@@ -476,7 +476,7 @@ extern "C" void hx_solve_default_opts(hx_solve_opts* o) {
   o->time_limit_s = 0.0;
   o->cancel = nullptr;
   o->nu_coarse = 2;
-  o->bicg_kappa = 0.7;
+  o->bicg_kappa = 0.0;
   o->coarse_velocity = 0;
 }
 

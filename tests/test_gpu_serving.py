@@ -1,6 +1,8 @@
 """GPU tests of the serving engine (hx_server_*): continuous admission of
-solve requests on several worker slots, device-memory admission, resident
-models across frequencies, cancellation, and results independent of the mix.
+solve requests on several worker slots, device-memory admission, the
+admission order (first come first served, or smallest first with a bound on
+the wait), resident models across frequencies, cancellation, and results
+independent of the mix.
 
 Every wavefield is also checked against its own equation: the oracle's
 assembled matrix (Eq. 3 rows, Eqs. 4-8, GA weights) applied on the CPU must
@@ -190,3 +192,56 @@ def test_cancel_queued_and_running_requests(otable):
     solo_srv.close()
     assert res[0]["status"] == 0
     assert np.linalg.norm(solo[0] - outs[2]) <= 1e-6 * np.linalg.norm(solo[0])
+
+
+def _one(shape, nrhs, seed):
+    v = synth.random_velocity(shape, seed, 1500.0, 3000.0)
+    nz, ny, nx = shape
+    h, npml = 25.0, 4
+    f = 1500.0 / (h * 8.0)
+    src = [(nx // 2, ny // 2, nz // 2 - r, r, 1.0) for r in range(nrhs)]
+    g = B.make_grid(shape, h, f, (npml,) * 6, float(v.max()))
+    return dict(model_id=seed, v=v, grid=g, src=src, nrhs=nrhs, f=f, h=h, npml=npml)
+
+
+@pytest.mark.parametrize("order,max_wait,first", [("smallest", 0.0, "small"), ("fifo", 0.0, "big"),
+                                                  ("smallest", 0.3, "big")])
+def test_admission_order(otable, order, max_wait, first):
+    # One slot, busy with a request that runs for 2 s; a large and then a small
+    # request queue behind it.  Smallest-first admits the small one first;
+    # first-come-first-served, or smallest-first once the large request has
+    # waited past the bound, admits the large one first.  Both still solve.
+    import time
+    blocker, big, small = _one((30, 28, 26), 1, 61), _one((34, 34, 34), 3, 62), _one((22, 22, 22), 1, 63)
+    srv = B.Server(otable[1], slots=1, order=order, max_wait_s=max_wait)
+    outs = {k: np.zeros((r["nrhs"],) + r["v"].shape, dtype=np.complex128)
+            for k, r in (("blocker", blocker), ("big", big), ("small", small))}
+    t_b = srv.submit(blocker["grid"], blocker["v"], blocker["src"], 1, outs["blocker"], model_id=61,
+                     tol=1e-30, max_outer=100000, time_limit_s=2.0)
+    t0 = time.time()
+    while srv.stats()["max_concurrent"] < 1:        # the blocker has started
+        assert time.time() - t0 < 60.0
+        time.sleep(0.02)
+    sub, tick = {}, {}
+    for k, r in (("big", big), ("small", small)):
+        sub[k] = time.perf_counter()
+        tick[k] = srv.submit(r["grid"], r["v"], r["src"], r["nrhs"], outs[k], model_id=r["model_id"])
+        time.sleep(0.4)
+    rb = srv.wait(t_b, timeout=60.0)
+    res = {k: srv.wait(tick[k], timeout=120.0) for k in tick}
+    srv.close()
+    assert rb["status"] == -3                       # stopped by its time limit
+    start = {k: sub[k] + res[k]["queue_ms"] / 1e3 for k in res}
+    assert min(start, key=start.get) == first, (start, res)
+    for k, r in (("big", big), ("small", small)):
+        assert res[k]["status"] == 0
+        assert _residual(otable, r, outs[k]) <= 1e-9
+
+
+def test_server_config_errors(otable):
+    with pytest.raises(B.HxError) as e:
+        B.Server(otable[1], slots=1, order="largest")
+    assert e.value.code == -1
+    with pytest.raises(B.HxError) as e:
+        B.Server(otable[1], slots=1, order="smallest", max_wait_s=-1.0)
+    assert e.value.code == -1

@@ -111,7 +111,7 @@ def test_batch_invariance(ctx, otable):
         assert M.rel_l2(alone[0], batch[k]) <= 1e-9
 
 
-@pytest.mark.parametrize("opts", [{"bicg_kappa": 0.0}, {"bicg_kappa": 0.5}, {"coarse_velocity": 1}])
+@pytest.mark.parametrize("opts", [{"bicg_kappa": 0.7}, {"bicg_kappa": 0.5}, {"coarse_velocity": 1}])
 def test_solver_options_reach_the_oracle_residual(ctx, otable, opts):
     # The omega safeguard and the averaged coarse velocity change only the
     # iterates: on a small sharp-contrast model (bodies and lens) the wavefield

@@ -5,6 +5,10 @@ sm_103a.  Needs nvcc, no GPU.
 * st32_kernel with 1 or 2 RHS per CTA (the configurations of the 1- and
   2-RHS solves): no stack frame, no spills, at most 128 registers (two CTAs
   of 256 threads per SM);
+* zm_frame_kernel (the PML rows of the tensor-copy kernel, all modes, with
+  and without the shift): no stack frame, no spills, at most 168 registers
+  (three CTAs of 128 threads per SM; its register window of four planes
+  spilled at the 128-register cap of four CTAs);
 * direct_stencil_k without a heterogeneous medium (every coarse multigrid
   level): no stack frame, no spills.  A stack frame here once came from an
   out-of-line call that took the row's 27 coefficients by address, and it
@@ -72,3 +76,15 @@ def test_coarse_level_kernel_budget(tmp_path):
             n += 1
             assert r.get("stack") == 0 and r.get("spill") == 0, (name, r)
     assert n == 8                                   # 2 precisions x 4 modes
+
+
+def test_frame_kernel_budget(tmp_path):
+    n = 0
+    for src in ("hx_zmarch_apply.cu", "hx_zmarch_residual.cu", "hx_zmarch_jacobi.cu"):
+        for name, r in _resources(src, tmp_path).items():
+            if "zm_frame_kernel" not in name:
+                continue
+            n += 1
+            assert r.get("stack") == 0 and r.get("spill") == 0, (name, r)
+            assert r.get("regs", 999) <= 168, (name, r)
+    assert n == 6                                   # 3 modes x (shift, no shift)
