@@ -65,7 +65,7 @@ FP64_FLOPS_PER_POINT = 40
 # Serving leg: the admission's bound on how long a large request is passed
 # over, the omega safeguard of the served solves, and the longest span of the
 # Poisson arrivals.
-SERVE_MAX_WAIT_S = 120.0
+SERVE_MAX_WAIT_S = 240.0
 SERVE_KAPPA = 0.7
 SERVE_MAX_SPAN_S = 600.0
 
