@@ -63,7 +63,9 @@ model both reduce to the GA / second-form operator; with weights that do not
 depend on the row (the non-adaptive G4 / Gm stencils) and no PML, the first
 mass form is the transpose of the second (M1 = W diag(m) = (diag(m) W)^T
 with W symmetric); a pure-Python loop over rows and stencil points on tiny
-grids gives the same rows (GAm averages, class stencils of Eq. 4).
+grids gives the same rows (GAm averages, class stencils of Eq. 4); with a
+table linear in 1/G and 1/G quadratic along x, u0 + c x^2, GAm's row at
+column x equals the Eq. 4 classes at the closed-form mean u0 + c (x^2 + 2/3).
 
 Pins (tests/test_oracle_operator.py): interior symbol == m J - 2X/h^2 on a
 periodic box (Eq. vtilde, independent formulas); stiffness annihilates

@@ -107,3 +107,38 @@ def test_unknown_variant_is_refused(table):
         O.row_coefficients(v, 25.0, 5.0, prof, T, nodes, weights="G4")
     with pytest.raises(ValueError):
         O.row_coefficients(v, 25.0, 5.0, prof, T, nodes, mass_form=3)
+
+
+def test_gam_weights_are_the_table_at_the_stencil_mean_of_a_quadratic_inverse_g():
+    # With a table linear in 1/G the interpolation is exact, so GAm's weights at
+    # a row are the table at the mean of 1/G over its 27 stencil points.  For
+    # 1/G quadratic along x, u = u0 + c x^2, that mean at column x is
+    # u0 + c (x^2 + 2/3), since each of the offsets -1, 0, 1 carries 9 of the 27
+    # points.  A 7-point mean (2/7), a mean without the corners or without the
+    # row itself, or a divisor other than 27 each miss it by about 1e-3 of the
+    # coefficients.  The row's classes then follow from Eq. 4 through
+    # interior_class_coefficients (no PML, so every row is an interior row).
+    nodes = np.linspace(0.0, 0.4, 41)
+    a = np.array([0.7, 0.2, 0.1, 0.5, 0.05, 0.02, 0.01])
+    b = np.array([-0.8, 0.5, 0.3, 0.4, -0.1, 0.05, 0.02])
+    T = a[None, :] + b[None, :] * nodes[:, None]
+    f, h, beta = 5.0, 25.0, 0.3
+    nz, ny, nx = 5, 5, 9
+    u0, c = 0.12, 0.004
+    xc = np.arange(nx) - 4.0
+    u = u0 + c * xc ** 2
+    v = np.broadcast_to((f * h / u)[None, None, :], (nz, ny, nx)).astype(np.float64)
+    prof = O.profiles_for(v.shape, h, (0,) * 6, float(v.max()), 1e-3)
+    rows = [ix + nx * (iy + ny * iz) for iz in range(1, nz - 1) for iy in range(1, ny - 1)
+            for ix in range(1, nx - 1)]
+    coef, ok = O.row_coefficients(v, h, f, prof, T, nodes, rows=rows, weights="GAm", beta=beta)
+    assert ok.all()
+    cls = np.array([abs(s[0]) + abs(s[1]) + abs(s[2]) for s in O.OFFSETS])
+    for r, row in enumerate(rows):
+        ix = row % nx
+        w7 = a + b * (u0 + c * (xc[ix] ** 2 + 2.0 / 3.0))
+        want = np.array(O.interior_class_coefficients(w7, h, 2.0 * np.pi * f, f * h / u[ix], beta=beta))
+        np.testing.assert_allclose(coef[r], want[cls], rtol=1e-12, atol=0)
+    # the same rows with GA use the row's own 1/G and differ at this size
+    ga, _ = O.row_coefficients(v, h, f, prof, T, nodes, rows=rows, weights="GA", beta=beta)
+    assert np.max(np.abs(ga - coef)) > 1e-4 * np.max(np.abs(coef))
