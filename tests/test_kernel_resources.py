@@ -55,8 +55,22 @@ def _resources(src, tmp_path):
     return res
 
 
-def test_complex64_stencil_budget(tmp_path):
-    res = _resources("hx_stencil32.cu", tmp_path)
+_SOURCES = ("hx_stencil32.cu", "hx_galerkin.cu", "hx_zmarch_apply.cu", "hx_zmarch_residual.cu",
+            "hx_zmarch_jacobi.cu")
+
+
+@pytest.fixture(scope="module")
+def resources(tmp_path_factory):
+    """ptxas reports of the checked translation units, compiled in parallel."""
+    from concurrent.futures import ThreadPoolExecutor
+    tmp = tmp_path_factory.mktemp("ptxas")
+    _nvcc()
+    with ThreadPoolExecutor(max_workers=len(_SOURCES)) as ex:
+        return dict(zip(_SOURCES, ex.map(lambda src: _resources(src, tmp), _SOURCES)))
+
+
+def test_complex64_stencil_budget(resources):
+    res = resources["hx_stencil32.cu"]
     n = 0
     for name, r in res.items():
         m = re.search(r"st32_kernelILi(\d)ELi(\d)ELi(\d)E", name)
@@ -68,8 +82,8 @@ def test_complex64_stencil_budget(tmp_path):
     assert n == 6                                   # 3 modes x (1, 2 RHS per CTA)
 
 
-def test_coarse_level_kernel_budget(tmp_path):
-    res = _resources("hx_galerkin.cu", tmp_path)
+def test_coarse_level_kernel_budget(resources):
+    res = resources["hx_galerkin.cu"]
     n = 0
     for name, r in res.items():
         if re.search(r"direct_stencil_kI[fd]Li\dELb0E", name):
@@ -78,10 +92,10 @@ def test_coarse_level_kernel_budget(tmp_path):
     assert n == 8                                   # 2 precisions x 4 modes
 
 
-def test_frame_kernel_budget(tmp_path):
+def test_frame_kernel_budget(resources):
     n = 0
     for src in ("hx_zmarch_apply.cu", "hx_zmarch_residual.cu", "hx_zmarch_jacobi.cu"):
-        for name, r in _resources(src, tmp_path).items():
+        for name, r in resources[src].items():
             if "zm_frame_kernel" not in name:
                 continue
             n += 1
