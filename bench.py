@@ -31,7 +31,9 @@ Also reported on the same JSON line:
                point*RHS/s, the failed requests with status and times;
   cpu_baseline the CPU oracle (banded LU, all host cores) on a bounded sample
                of the same workload: the 24^3 corner-free sub-grid around the
-               source with the same model, PML and frequency.
+               source with the same model, PML and frequency; with its CSR
+               matvec on the full grid and the band storage a full-size banded
+               LU would need (extras).
 
 --impl reference runs the oracle alone (rank 0), on the same metric.
 Multi-GPU: one process per GPU (torchrun); every rank solves its own copy of
@@ -176,6 +178,43 @@ def oracle_rate(budget_s=12.0, n=24):
     desc = (f"banded LU (scipy solve_banded, LAPACK gbsv) + CSR assembly of a {n}^3 sub-grid of the "
             f"linear-gradient model (same h, f, v law, {wl.npml[0]}-node PML), {reps} solves")
     return rate, el, reps, desc, os.cpu_count()
+
+
+def banded_lu_bytes(nx, ny, nz):
+    """Band storage of LAPACK's banded LU (gbsv) for the 27-point operator in
+    x-fastest order: half-bandwidth nx*ny + nx + 1, (2 kl + ku + 1) rows of N
+    complex128 values."""
+    kl = nx * ny + nx + 1
+    return (3 * kl + 1) * nx * ny * nz * 16
+
+
+def oracle_extras():
+    """The oracle's CSR matvec on the full linear-gradient grid (scipy, one
+    thread) and the band storage that rules out the oracle's banded LU on the
+    full-size workloads."""
+    from oracle import operator as O
+    from oracle import weights as W
+    from paper_2108_08730_gb300 import synth
+    import numpy as np
+    nodes, T = W.fit_table()
+    wl = synth.linear_gradient()
+    prof = O.profiles_for(wl.shape, wl.h, wl.npml, wl.v_ref, wl.r_coef)
+    t0 = time.perf_counter()
+    A = O.assemble_csr(wl.v, wl.h, wl.f, prof, T, nodes)
+    t_asm = time.perf_counter() - t0
+    x = np.random.default_rng(0).standard_normal(A.shape[0]) + 0j
+    t0 = time.perf_counter()
+    n = 0
+    while n < 3 or time.perf_counter() - t0 < 2.0:
+        A @ x
+        n += 1
+    t_mv = (time.perf_counter() - t0) / n
+    sizes = {"linear_gradient 101^3": (101, 101, 101), "sharp_contrast 201x201x101": (201, 201, 101),
+             "tectonic 401x401x187": (401, 401, 187)}
+    return {"csr_matvec": {"workload": "linear_gradient 101^3 (oracle CSR, scipy, 1 thread)",
+                           "mpoint_per_s": round(wl.n_points / t_mv / 1e6, 3), "ms": round(1e3 * t_mv, 1),
+                           "assembly_s": round(t_asm, 2)},
+            "banded_lu_band_storage_gb": {k: round(banded_lu_bytes(*v) / 1e9, 1) for k, v in sizes.items()}}
 
 
 def run_reference(args):
@@ -437,7 +476,8 @@ def run_gpu(args):
     cpu = None
     if world == 1 and not args.no_cpu:
         r, el, reps, desc, cores = oracle_rate()
-        cpu = {"value": round(r, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = {"value": round(r, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "extras": oracle_extras()}
 
     serving = None
     if world == 1 and args.serve_requests > 0:
